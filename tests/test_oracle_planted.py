@@ -1,0 +1,66 @@
+"""Each test plants one plausible mistake in the CPU oracle (monkeypatched, on the CPU) and
+checks that at least one pin in test_oracle_pins fails, so the pins are known to be able
+to see that kind of error."""
+import os
+
+import numpy as np
+import pytest
+
+import oracle.mdp_oracle as mo
+from tests import test_oracle_pins as pins
+
+
+def _fails(fn, *args):
+    with pytest.raises(AssertionError):
+        fn(*args)
+
+
+def test_transposed_transition_is_caught(monkeypatch):
+    def bad(mdp, a, v):
+        if mdp.kind == "dense":
+            return mdp.P[a].astype(np.float64).T @ v
+        return mo.__dict__["_orig_ta"](mdp, a, v)
+    monkeypatch.setitem(mo.__dict__, "_orig_ta", mo.transition_apply)
+    monkeypatch.setattr(mo, "transition_apply", bad)
+    _fails(pins.test_constant_cost_every_action_ties, "vi")
+
+
+def test_dropped_discount_is_caught(monkeypatch):
+    def bad(mdp, v):  # g + P v: the discount factor left out
+        return np.stack([mdp.g[a] + mo.transition_apply(mdp, a, v) for a in range(mdp.A)])
+    monkeypatch.setattr(mo, "q_values", bad)
+    _fails(pins.test_single_state, "vi")
+
+
+def test_argmax_instead_of_argmin_is_caught(monkeypatch):
+    monkeypatch.setattr(mo, "greedy_policy", lambda Q: np.argmax(np.where(np.isfinite(Q), Q, -np.inf), axis=0).astype(np.int32))
+    _fails(pins.test_golden_examples, os.path.join(pins.GOLDEN, "two_state_switch.json"), "pi")
+
+
+def test_wrong_sign_in_gram_schmidt_is_caught(monkeypatch):
+    orig_lsq = mo._lsq
+
+    def bad_lsq(H, beta):
+        y = orig_lsq(H, beta)
+        return -y if H.shape[1] > 1 else y
+    monkeypatch.setattr(mo, "_lsq", bad_lsq)
+    _fails(pins.test_gmres_unrestarted_is_exact_within_n_steps, "dense")
+
+
+def test_restart_that_drops_the_base_is_caught(monkeypatch):
+    src = mo._gmres_inner
+
+    def bad(J, g_pi, V_k, Phi_k, threshold, W, max_steps, st):
+        # restart from V_k every cycle (forgets the progress of earlier cycles)
+        return src(J, g_pi, V_k, Phi_k, threshold, W, min(max_steps, W), st)
+    monkeypatch.setattr(mo, "_gmres_inner", bad)
+    _fails(pins.test_gmres_restarted_converges_to_lu, 2)
+
+
+def test_policy_matrix_with_wrong_row_index_is_caught(monkeypatch):
+    orig = mo.policy_matrix
+
+    def bad(mdp, pi):
+        return orig(mdp, np.roll(np.asarray(pi), 1))
+    monkeypatch.setattr(mo, "policy_matrix", bad)
+    _fails(pins.test_golden_examples, os.path.join(pins.GOLDEN, "three_state_reset.json"), "igmres")
