@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark: iGMRES-PI (Alg. 2) solves per second on the paper-scale dense MDP.
+
+Workload: S = 10^4 states, A = 8 actions, dense row-stochastic P_a stored in FP32 (rows
+Dirichlet(0.1)), costs U(0,1), gamma = 0.99; the mixed FP32 / double-float form solved to
+||T(v) - v||_inf <= 1e-8 with alpha = 0.1, GMRES restart W = 30.  One step = one whole
+solve from V_0 = 0 with the MDP resident in HBM (3.2 GB of P: every sweep streams more than
+the 129 MB L2, so no flush is needed between steps).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torch.distributed.run, one rank per GPU; every rank solves its own copy
+of the workload (independent problems, no collective on the data path) and rank 0 prints
+one JSON line with the whole-job rate.  --impl reference times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "MDP solves/s to ||T(v)-v||_inf<=1e-8, p50/p99 latency; Bellman-op HBM GB/s"
+S_, A_, GAMMA, TOL, ALPHA, W_ = 10000, 8, 0.99, 1e-8, 0.1, 30
+WORKLOAD = ("paper-scale dense MDP: S=10000, A=8, FP32 P_a rows Dirichlet(0.1), g~U(0,1), "
+            "gamma=0.99; iGMRES-PI mixed FP32/double-float, alpha=0.1, W=30, tol 1e-8")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true")
+    return ap.parse_args()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sweep_algorithmic_bytes(S, A):
+    """Bytes one full Bellman sweep must move: every P_a entry (FP32), the costs as
+    double-float pairs, v read once (8 B/state) and pi, Tv, Phi written (4 + 8 + 4 B)."""
+    return A * S * S * 4 + A * S * 8 + S * 8 + S * 16
+
+
+def matvec_algorithmic_bytes(S):
+    """One P^pi matvec in FP32: row pi(s) of P_{pi(s)} per state, pi, x read, w written."""
+    return S * S * 4 + S * (4 + 4 + 4)
+
+
+def source_hash():
+    h = hashlib.sha256()
+    for rel in ["paper_2211_04299_gb300/csrc/sweep.cu", "paper_2211_04299_gb300/csrc/mdp_internal.cuh"]:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def traffic_for(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
+    kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get(kernel_key)
+        if e and e.get("source_hash") == source_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.file.flush()
+        rows = [ln.split(",") for ln in open(self.file.name).read().strip().splitlines()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, r[5:9]):
+                if "Active" in val and "Not" not in val:
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle arm
+def oracle_sample(syn_m, counts):
+    """Time a bounded sample of the oracle on the workload: one Bellman sweep and one outer
+    iteration of Alg. 2 (K=1, which ends with one more sweep); scale to a whole solve with
+    the oracle's own outer-iteration count for this workload."""
+    import oracle
+    t0 = time.perf_counter()
+    oracle.bellman(syn_m, np.zeros(syn_m.S))
+    t_sweep = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    oracle.gmres_policy_iteration(syn_m, alpha=ALPHA, W=W_, tol=TOL, K=1)
+    t_k1 = time.perf_counter() - t0
+    n_outer = int(counts["outer"]) + 1  # sweeps of a whole solve (the last one only tests)
+    t_body = max(t_k1 - 2 * t_sweep, 0.0)
+    t_solve = n_outer * t_sweep + (n_outer - 1) * t_body
+    return t_solve, t_k1 + t_sweep
+
+
+def oracle_counts():
+    with open(os.path.join(ROOT, "oracle", "reference_counts.json")) as f:
+        return json.load(f)["config2"]
+
+
+def cores_used():
+    try:
+        import threadpoolctl
+        info = threadpoolctl.threadpool_info()
+        n = max([i.get("num_threads", 1) for i in info] or [1])
+        return int(n)
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def reference_arm(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import mdp_synth
+    import oracle
+    counts = oracle_counts()
+    m = oracle.from_synth(mdp_synth.config(2))
+    for _ in range(args.warmup):
+        oracle_sample(m, counts)
+    times = []
+    wall = 0.0
+    for _ in range(args.steps):
+        t_solve, t_real = oracle_sample(m, counts)
+        times.append(t_solve)
+        wall += t_real
+    total = sum(times)
+    value = args.steps / total
+    cores = cores_used()
+    sample = (f"per step: one Bellman sweep + one outer iteration of Alg. 2 (K=1) on the "
+              f"full workload, scaled to a whole solve with the oracle's own count of "
+              f"{counts['outer']} outer iterations")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return reference_arm(args)
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    from paper_2211_04299_gb300 import build
+    build.build()
+    import paper_2211_04299_gb300 as mg
+    import mdp_synth
+
+    syn = mdp_synth.config(2)
+    S, A = syn.S, syn.A
+    h = mg.from_synth(syn)
+    stream = torch.cuda.current_stream()
+    h.set_stream(stream)
+    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed")
+    v_out = torch.empty(S, dtype=torch.float64, device="cuda")
+    pi_out = torch.empty(S, dtype=torch.int32, device="cuda")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    for _ in range(max(3, args.warmup)):
+        mg.ipi_solve(h, o, v_out=v_out, pi_out=pi_out)
+    torch.cuda.synchronize()
+    barrier()
+
+    h.set_timing(True)
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stats = []
+    torch.cuda.synchronize()
+    barrier()
+    ev[0].record(stream)
+    for i in range(args.steps):
+        _, _, st = mg.ipi_solve(h, o, v_out=v_out, pi_out=pi_out)
+        ev[i + 1].record(stream)
+        stats.append(st)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    h.set_timing(False)
+    elapsed_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    value = world * args.steps / (elapsed_ms / 1000.0)
+
+    ok = all(s["status"] == 0 and s["residual_inf"] <= TOL for s in stats)
+    sweeps = sum(s["timed_sweeps"] for s in stats)
+    sweep_ms = sum(s["sweep_ms"] for s in stats) / max(1, sweeps)
+    mvs = sum(s["timed_matvecs"] for s in stats)
+    mv_ms = sum(s["matvec_ms"] for s in stats) / max(1, mvs)
+    peak, peak_kind = peaks()
+    sb = sweep_algorithmic_bytes(S, A)
+    mb = matvec_algorithmic_bytes(S)
+    sweep_gbs = sb / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
+    mv_gbs = mb / (mv_ms * 1e-3) / 1e9 if mv_ms > 0 else 0.0
+    launches = int(sum(s["launches"] for s in stats))
+    per_solve_sweep_ms = sweep_ms * sweeps / args.steps
+    per_solve_mv_ms = mv_ms * mvs / args.steps
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(3, args.warmup),
+        "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "mixed: f32 P/Krylov, double-float (2xf32) values, f64 Givens",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "S": S, "A": A, "gamma": GAMMA, "tol": TOL,
+                   "alpha": ALPHA, "restart": W_, "precision": "mixed",
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (P is 3.2 GB, L2 129 MB); no flush"},
+        "converged": ok,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
+        "per_solve": {"outer": stats[-1]["outer"], "inner": stats[-1]["inner"],
+                      "sweeps": stats[-1]["sweeps"], "matvecs": stats[-1]["matvecs"],
+                      "sweep_ms": per_solve_sweep_ms, "matvec_ms": per_solve_mv_ms},
+        "bellman_sweep": {"ms": sweep_ms, "gbs": sweep_gbs, "sweeps_per_s": 1000.0 / sweep_ms if sweep_ms else 0.0,
+                          "algorithmic_bytes": sb},
+        "pi_matvec": {"ms": mv_ms, "gbs": mv_gbs, "algorithmic_bytes": mb, "frac": mv_gbs / peak},
+        "roofline": {"bound": "hbm", "kernel": "sweep_dense_kernel<float,ArDF,8>",
+                     "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
+                     "frac": sweep_gbs / peak, "peak_source": peak_kind,
+                     "traffic": traffic_for("sweep_dense_df_cfg2")},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    # end to end through the host-pointer API: upload P, g from pinned memory, solve, copy back
+    if not args.no_e2e:
+        P_pin = torch.from_numpy(syn.P).pin_memory()
+        g_np = np.ascontiguousarray(syn.g)
+        Pn = P_pin.numpy()
+        v_h = np.empty(S)
+        pi_h = np.empty(S, np.int32)
+        e2e_steps = min(args.steps, 5)
+        mg.mdp_load_dense(h, Pn, g_np)
+        mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            mg.mdp_load_dense(h, Pn, g_np)
+            mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * e2e_steps / float(tt.item()), "unit": "solves/s",
+                       "h2d_bytes_per_step": int(Pn.nbytes + g_np.nbytes),
+                       "d2h_bytes_per_step": int(v_h.nbytes + pi_h.nbytes), "steps": e2e_steps}
+        del P_pin
+
+    # the plain per-instance FP64 form on the same MDP (P widened exactly to FP64)
+    if not args.no_fp64:
+        syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="dense",
+                                   P=syn.P.astype(np.float64))
+        h64 = mg.from_synth(syn64)
+        h64.set_stream(stream)
+        o64 = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="fp64")
+        mg.ipi_solve(h64, o64, v_out=v_out, pi_out=pi_out)
+        torch.cuda.synchronize()
+        n64 = 3
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(n64):
+            _, _, st64 = mg.ipi_solve(h64, o64, v_out=v_out, pi_out=pi_out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1) / n64
+        line["fp64_plain"] = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_solve": ms64,
+                              "outer": st64["outer"], "inner": st64["inner"],
+                              "converged": st64["status"] == 0}
+        h64.close()
+        del syn64
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        counts = oracle_counts()
+        m = oracle.from_synth(syn)
+        t_solve, t_real = oracle_sample(m, counts)
+        line["cpu_baseline"] = {
+            "value": 1.0 / t_solve, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+            "sample": (f"one Bellman sweep + one outer iteration of Alg. 2 on the full workload "
+                       f"({t_real:.1f} s of CPU), scaled to a whole solve with the oracle's own "
+                       f"{counts['outer']} outer iterations")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,202 @@
+/*
+ * mdpgpu.h - C ABI of the GB300 (sm_103a) library for inexact GMRES policy iteration
+ * (iGMRES-PI) on finite discounted-cost Markov decision processes.
+ *
+ * Problem (paper Sec. 2): a finite MDP {S, A, P, g, gamma} with states 0..S-1 and actions
+ * 0..A-1 (the paper counts from 1), transition rows p_{ss'}(a) that sum to one, bounded
+ * stage costs g(s, a), discount gamma in (0, 1) and nonempty allowed-action sets A(s).
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: MDP_OK (0) on success, a negative MDP_E* code on failure;
+ *     mdp_last_error() then returns a message (thread-local, valid until the next call on
+ *     the same thread).  MDP_ENOCONV still writes the last iterate, policy and stats.
+ *   - Plain entry points take HOST pointers: inputs are copied to the device, outputs are
+ *     copied back before the call returns (the call synchronises the handle's stream).
+ *     The *_dev entry points take DEVICE pointers, enqueue on the handle's stream and
+ *     return without a host-side wait except where a scalar decides control flow.
+ *   - Layouts are row-major C arrays: P[a][s][s'], col/val[a][s][j], g[a][s], mask[s][a].
+ *   - A handle owns device copies of P, g and mask plus all solver workspace; the caller
+ *     keeps ownership of every pointer it passes.  One handle serves one stream at a time;
+ *     distinct handles may be used from distinct threads.
+ *   - Every device wait inside the library is bounded; nothing here spins without limit.
+ */
+#ifndef MDPGPU_H
+#define MDPGPU_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct mdp_s* mdp_t;
+
+enum mdp_status {
+  MDP_OK = 0,
+  MDP_EINVAL = -1,    /* bad argument or malformed MDP (see mdp_last_error) */
+  MDP_ENOMEM = -2,    /* device allocation failed */
+  MDP_ENOCONV = -3,   /* iteration cap reached before the stopping rule held */
+  MDP_EDEVICE = -4,   /* CUDA runtime error */
+  MDP_ETIMEOUT = -5,  /* a bounded device wait ran out */
+  MDP_EBREAKDOWN_INFO = 1 /* informational: GMRES met a (lucky) breakdown; result valid */
+};
+
+enum mdp_dtype { MDP_F32 = 0, MDP_F64 = 1 };
+
+/* Arithmetic of the solvers.
+ *   MDP_PREC_FP64  : every vector and sum in FP64 (needs P stored in FP64 for full accuracy;
+ *                    FP32-stored P is widened exactly on the fly).
+ *   MDP_PREC_MIXED : P (FP32) and the Krylov vectors in FP32 with FP32 accumulation; the
+ *                    value vector, the Bellman sweep that gives ||T(v)-v||_inf and the final
+ *                    polish sweep in double-float (two-FP32) arithmetic, accurate to about
+ *                    2^-48 relative; the Hessenberg least-squares (Givens) in FP64. */
+enum mdp_precision { MDP_PREC_FP64 = 0, MDP_PREC_MIXED = 1 };
+
+/* ---------------------------------------------------------------------------- handles */
+
+/* Dense MDP (Sec. 2).  P: A*S*S values of type p_dtype, P[a][s][s'] = p_{ss'}(a); every
+ * row must be nonnegative, finite and sum to 1 within 1e-5 (F32) or 1e-12 (F64) absolute.
+ * g: A*S finite FP64 costs, g[a][s] = g(s, a).  gamma in (0, 1).  mask: NULL (all actions
+ * allowed) or S*A bytes, nonzero = allowed, with at least one allowed action per state.
+ * On success *out holds a new handle.  Errors: MDP_EINVAL (bad sizes/values; nothing is
+ * allocated), MDP_ENOMEM, MDP_EDEVICE. */
+int mdp_create_dense(int64_t S, int32_t A, const void* P, int p_dtype, const double* g,
+                     double gamma, const uint8_t* mask, mdp_t* out);
+
+/* ELL-sparse MDP: row (a, s) lists k pairs (col[a][s][j], val[a][s][j]); p_{ss'}(a) is the
+ * sum of val over the j with col = s'.  1 <= k <= S, 0 <= col < S, val as P above. */
+int mdp_create_ell(int64_t S, int32_t A, int32_t k, const int32_t* col, const void* val,
+                   int val_dtype, const double* g, double gamma, const uint8_t* mask,
+                   mdp_t* out);
+
+/* Same as the two above with DEVICE input pointers (copied device-to-device).  Inputs are
+ * validated on the device; no host copy of P is made. */
+int mdp_create_dense_dev(int64_t S, int32_t A, const void* P, int p_dtype, const double* g,
+                         double gamma, const uint8_t* mask, mdp_t* out);
+int mdp_create_ell_dev(int64_t S, int32_t A, int32_t k, const int32_t* col, const void* val,
+                       int val_dtype, const double* g, double gamma, const uint8_t* mask,
+                       mdp_t* out);
+
+/* Replace the transition data and costs of an existing handle with new HOST arrays of the
+ * same shape and dtype (no allocation; validation as at creation).  This is the per-request
+ * upload path of a client that reuses one handle for a stream of same-shaped MDPs. */
+int mdp_load_dense(mdp_t h, const void* P, const double* g);
+int mdp_load_ell(mdp_t h, const int32_t* col, const void* val, const double* g);
+
+void mdp_destroy(mdp_t h);
+
+/* Run the handle's work on a caller-provided cudaStream_t (passed as void*); NULL selects
+ * the handle's own stream. */
+int mdp_set_stream(mdp_t h, void* cuda_stream);
+
+/* Shape query: any pointer may be NULL. kind: 0 dense, 1 ELL. */
+int mdp_info(mdp_t h, int64_t* S, int32_t* A, int32_t* k, int32_t* kind, int32_t* dtype,
+             double* gamma);
+
+/* Device bytes held by the handle (transition data, costs, workspace). */
+int64_t mdp_device_bytes(mdp_t h);
+
+/* ---------------------------------------------------------------------------- options */
+
+typedef struct {
+  double alpha;        /* forcing term of the inner stopping rule (Sec. 3, Eq. stopping_rule) */
+  double tol;          /* outer stop: ||T(v) - v||_inf <= tol */
+  int32_t restart;     /* GMRES restart length W (1..64) */
+  int32_t max_outer;   /* cap K on outer iterations (Alg. 2) */
+  int32_t max_inner;   /* cap on Arnoldi steps per outer iteration */
+  int32_t precision;   /* enum mdp_precision */
+  int32_t opi_W;       /* OPI: applications of T^pi per outer step (Sec. 2.1) */
+  int32_t pi_inner_tol_exp; /* PI: relative GMRES tolerance 10^-x for "exact" evaluation */
+  const double* v0;    /* initial V_0 (host for host calls, device for *_dev); NULL = 0 */
+} mdp_opts;
+
+/* alpha 0.1, tol 1e-8, restart 30, max_outer 100, max_inner 3000, precision MIXED,
+ * opi_W 50, pi_inner_tol_exp 13, v0 NULL. */
+mdp_opts mdp_opts_default(void);
+
+typedef struct {
+  int32_t outer;        /* outer iterations done */
+  int32_t inner;        /* Arnoldi steps (all outer iterations) */
+  int32_t restarts;     /* GMRES restarts */
+  int32_t sweeps;       /* Bellman sweeps (full, all actions) */
+  int32_t matvecs;      /* P^pi matrix-vector products (incl. T^pi applications) */
+  int32_t status;       /* enum mdp_status of the solve */
+  double residual_inf;  /* ||T(V_K) - V_K||_inf of the returned iterate */
+  double seconds;       /* wall time of the call */
+  double bytes;         /* algorithmic HBM bytes moved by the solve's kernels */
+  double sweep_ms;      /* summed device time of the Bellman sweep launches (timing on) */
+  double matvec_ms;     /* summed device time of the P^pi matvec launches (timing on) */
+  int32_t timed_sweeps; /* sweep launches covered by sweep_ms */
+  int32_t timed_matvecs;/* matvec launches covered by matvec_ms */
+  int32_t launches;     /* kernels launched by the call */
+  int32_t reserved;
+} mdp_stats;
+
+/* When on (nonzero), every Bellman-sweep and matvec launch is bracketed by CUDA events on
+ * the handle's stream and its device time is added to mdp_stats.sweep_ms / matvec_ms. */
+int mdp_set_timing(mdp_t h, int on);
+
+/* ---------------------------------------------------------------------------- operators */
+
+/* One Bellman sweep (Sec. 2; Alg. 2 lines "pi_k <- GreedyPolicy(V_k)" and "Phi_k"):
+ *   Q(s,a) = g(s,a) + gamma * sum_s' p_{ss'}(a) v(s'),  pi(s) = argmin_{a in A(s)} Q(s,a)
+ *   (lowest index among exact minima), Tv(s) = Q(s, pi(s)), res_inf = ||Tv - v||_inf.
+ * Host pointers v[S] (in), Tv[S], pi[S] (out, may be NULL), res_inf (out, may be NULL).
+ * precision selects FP64 or double-float accumulation (see enum mdp_precision). */
+int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res_inf,
+                  int32_t precision);
+
+/* Device-pointer form; margin[S] (may be NULL) receives Q2(s) - Q1(s), the gap between the
+ * two smallest Q values (+inf with one allowed action).  *res_inf is a HOST pointer and the
+ * call waits for it when it is not NULL. */
+int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double* margin,
+                      double* res_inf, int32_t precision);
+
+/* Inexact policy evaluation (Alg. 2 inner loop for a fixed pi): restarted GMRES(W) on
+ * (I - gamma P^pi) V = g^pi from v0 (NULL = 0) until ||g^pi - (I - gamma P^pi) V||_inf <=
+ * target_inf or opts->max_inner steps.  Host pointers pi[S], v0[S], v_out[S]. */
+int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double target_inf,
+                      const mdp_opts* opts, double* v_out, mdp_stats* stats);
+int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double target_inf,
+                          const mdp_opts* opts, double* v_out, mdp_stats* stats);
+
+/* ---------------------------------------------------------------------------- solvers */
+
+/* iGMRES-PI, Alg. 2: for k < max_outer: pi_k = GreedyPolicy(V_k), Phi_k = T(V_k) - V_k;
+ * stop when ||Phi_k||_inf <= tol; otherwise GMRES(W) on (I - gamma P^{pi_k}) V = g^{pi_k}
+ * from V_k while ||g^{pi_k} - (I - gamma P^{pi_k}) V_{k+1}||_inf > alpha ||Phi_k||_inf.
+ * Returns v = T(V_K), pi = GreedyPolicy(V_K) and ||Phi_K||_inf in stats.  Host pointers. */
+int ipi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+              mdp_stats* stats);
+int ipi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+                  mdp_stats* stats);
+
+/* VI (Sec. 2.1, Eq. VI_optimalcost): V <- T V until ||T V - V||_inf <= tol. */
+int vi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out, mdp_stats* stats);
+int vi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+                 mdp_stats* stats);
+
+/* PI (Sec. 2.1): policy evaluation by GMRES to a relative residual 10^-pi_inner_tol_exp,
+ * then improvement, until ||T V - V||_inf <= tol or the policy repeats. */
+int pi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out, mdp_stats* stats);
+int pi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+                 mdp_stats* stats);
+
+/* OPI (Sec. 2.1): per outer step, W = opts->opi_W applications of T^{pi_k}, the first being
+ * the T V_k of the greedy sweep. */
+int opi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+              mdp_stats* stats);
+int opi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+                  mdp_stats* stats);
+
+/* Message for the last nonzero return on this thread ("" if none). */
+const char* mdp_last_error(void);
+
+/* Library version string. */
+const char* mdp_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MDPGPU_H */

@@ -1,0 +1,232 @@
+"""GB300 (sm_103a) inexact GMRES policy iteration for finite discounted-cost MDPs.
+
+Thin Python binding over the C ABI of libmdpgpu (include/mdpgpu.h).  Each function has the
+name of the C entry point it calls and only marshals arguments: numpy arrays go to the
+host-pointer entry points, CUDA torch tensors to the *_dev ones.  Every arithmetic step runs
+in the library's CUDA kernels; when the library is missing, importing a function raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _lib
+from ._lib import (MDP_F32, MDP_F64, MDP_PREC_FP64, MDP_PREC_MIXED, MDPError,  # noqa: F401
+                   mdp_opts, mdp_stats)
+
+__all__ = [
+    "MDPHandle", "mdp_create_dense", "mdp_create_ell", "bellman_apply", "policy_eval_gmres",
+    "ipi_solve", "vi_solve", "pi_solve", "opi_solve", "opts", "MDP_PREC_FP64",
+    "MDP_PREC_MIXED", "MDPError", "lib",
+]
+
+
+def lib():
+    return _lib.load()
+
+
+def _is_cuda(x) -> bool:
+    return getattr(x, "is_cuda", False)
+
+
+def _ptr(x):
+    """Address of a contiguous numpy array or CUDA tensor (None -> NULL)."""
+    if x is None:
+        return None
+    if _is_cuda(x):
+        if not x.is_contiguous():
+            raise ValueError("device tensors must be contiguous")
+        return C.c_void_p(x.data_ptr())
+    if not x.flags["C_CONTIGUOUS"]:
+        raise ValueError("host arrays must be C-contiguous")
+    return C.c_void_p(x.ctypes.data)
+
+
+def _check(code, where):
+    if code < 0 and code != _lib.MDP_ENOCONV:
+        raise MDPError(code, where)
+    return code
+
+
+def _dtype_code(arr) -> int:
+    name = str(arr.dtype)
+    if name.endswith("float32"):
+        return MDP_F32
+    if name.endswith("float64"):
+        return MDP_F64
+    raise TypeError(f"transition data must be float32 or float64, not {arr.dtype}")
+
+
+class MDPHandle:
+    """Owns an mdp_t; destroyed with the object (or explicitly with close())."""
+
+    def __init__(self, ptr, S, A, k, kind, dtype):
+        self._p = ptr
+        self.S, self.A, self.k, self.kind, self.dtype = S, A, k, kind, dtype
+
+    @property
+    def ptr(self):
+        if self._p is None:
+            raise ValueError("handle is closed")
+        return self._p
+
+    def close(self):
+        if self._p is not None:
+            lib().mdp_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_bytes(self) -> int:
+        return int(lib().mdp_device_bytes(self.ptr))
+
+    def set_stream(self, stream) -> None:
+        """stream: torch.cuda.Stream, an integer cudaStream_t, or None."""
+        s = getattr(stream, "cuda_stream", stream)
+        _check(lib().mdp_set_stream(self.ptr, C.c_void_p(s) if s else None), "mdp_set_stream")
+
+    def set_timing(self, on: bool) -> None:
+        _check(lib().mdp_set_timing(self.ptr, 1 if on else 0), "mdp_set_timing")
+
+
+def mdp_create_dense(P, g, gamma: float, mask=None) -> MDPHandle:
+    """P[a, s, s'] (A, S, S) float32/float64, g[a, s] (A, S) float64, mask[s, a] uint8."""
+    A, S, S2 = P.shape
+    if S != S2 or tuple(g.shape) != (A, S):
+        raise ValueError("P must be (A, S, S) and g (A, S)")
+    h = C.c_void_p()
+    fn = lib().mdp_create_dense_dev if _is_cuda(P) else lib().mdp_create_dense
+    _check(fn(S, A, _ptr(P), _dtype_code(P), _ptr(g), float(gamma), _ptr(mask), C.byref(h)),
+           "mdp_create_dense")
+    return MDPHandle(h, S, A, 0, "dense", _dtype_code(P))
+
+
+def mdp_create_ell(col, val, g, gamma: float, mask=None) -> MDPHandle:
+    """col/val[a, s, j] (A, S, k) int32 / float32|float64, g[a, s] (A, S) float64."""
+    A, S, k = val.shape
+    if tuple(col.shape) != (A, S, k) or tuple(g.shape) != (A, S):
+        raise ValueError("col/val must be (A, S, k) and g (A, S)")
+    h = C.c_void_p()
+    fn = lib().mdp_create_ell_dev if _is_cuda(val) else lib().mdp_create_ell
+    _check(fn(S, A, k, _ptr(col), _ptr(val), _dtype_code(val), _ptr(g), float(gamma),
+              _ptr(mask), C.byref(h)), "mdp_create_ell")
+    return MDPHandle(h, S, A, k, "ell", _dtype_code(val))
+
+
+def mdp_load_dense(h: MDPHandle, P, g) -> None:
+    _check(lib().mdp_load_dense(h.ptr, _ptr(P), _ptr(g)), "mdp_load_dense")
+
+
+def mdp_load_ell(h: MDPHandle, col, val, g) -> None:
+    _check(lib().mdp_load_ell(h.ptr, _ptr(col), _ptr(val), _ptr(g)), "mdp_load_ell")
+
+
+def opts(**kw) -> mdp_opts:
+    """mdp_opts with the library defaults, overridden by keyword (v0 must stay alive)."""
+    o = lib().mdp_opts_default()
+    for key, val in kw.items():
+        if key == "v0":
+            o.v0 = C.cast(_ptr(val), C.POINTER(C.c_double)) if val is not None else None
+        elif key == "precision" and isinstance(val, str):
+            o.precision = MDP_PREC_MIXED if val == "mixed" else MDP_PREC_FP64
+        else:
+            setattr(o, key, val)
+    return o
+
+
+def _prec(p) -> int:
+    if isinstance(p, str):
+        return MDP_PREC_MIXED if p == "mixed" else MDP_PREC_FP64
+    return int(p)
+
+
+def _new_like(h: MDPHandle, device, dtype):
+    if device:
+        import torch
+        tdt = torch.float64 if dtype == "f64" else torch.int32
+        return torch.empty(h.S, dtype=tdt, device="cuda")
+    return np.empty(h.S, dtype=np.float64 if dtype == "f64" else np.int32)
+
+
+def bellman_apply(h: MDPHandle, v, precision=MDP_PREC_MIXED, margin: bool = False):
+    """One Bellman sweep at v -> (Tv, pi, ||Tv - v||_inf[, margin])."""
+    dev = _is_cuda(v)
+    Tv, pi = _new_like(h, dev, "f64"), _new_like(h, dev, "i32")
+    res = C.c_double(0.0)
+    if dev:
+        mg = _new_like(h, True, "f64") if margin else None
+        _check(lib().bellman_apply_dev(h.ptr, _ptr(v), _ptr(Tv), _ptr(pi), _ptr(mg),
+                                       C.cast(C.pointer(res), C.c_void_p), _prec(precision)),
+               "bellman_apply_dev")
+        return (Tv, pi, res.value, mg) if margin else (Tv, pi, res.value)
+    if margin:
+        raise ValueError("margin output is available through device tensors only")
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    _check(lib().bellman_apply(h.ptr, _ptr(v), _ptr(Tv), _ptr(pi),
+                               C.cast(C.pointer(res), C.c_void_p), _prec(precision)),
+           "bellman_apply")
+    return Tv, pi, res.value
+
+
+def policy_eval_gmres(h: MDPHandle, pi, v0=None, target_inf: float = 1e-10, o=None):
+    """GMRES(W) policy evaluation -> (V, stats dict)."""
+    dev = _is_cuda(pi)
+    o = o or opts()
+    out = _new_like(h, dev, "f64")
+    st = mdp_stats()
+    fn = lib().policy_eval_gmres_dev if dev else lib().policy_eval_gmres
+    if not dev:
+        pi = np.ascontiguousarray(pi, dtype=np.int32)
+        v0 = None if v0 is None else np.ascontiguousarray(v0, dtype=np.float64)
+    _check(fn(h.ptr, _ptr(pi), _ptr(v0), float(target_inf), C.byref(o), _ptr(out), C.byref(st)),
+           "policy_eval_gmres")
+    return out, st.as_dict()
+
+
+def _solve(name: str, h: MDPHandle, o=None, device: bool = False, v_out=None, pi_out=None):
+    o = o or opts()
+    v = v_out if v_out is not None else _new_like(h, device, "f64")
+    pi = pi_out if pi_out is not None else _new_like(h, device, "i32")
+    st = mdp_stats()
+    dev = _is_cuda(v)
+    fn = getattr(lib(), name + ("_dev" if dev else ""))
+    _check(fn(h.ptr, C.byref(o), _ptr(v), _ptr(pi), C.byref(st)), name)
+    return v, pi, st.as_dict()
+
+
+def ipi_solve(h, o=None, device=False, v_out=None, pi_out=None):
+    """iGMRES-PI (Alg. 2) -> (v = T(V_K), pi, stats)."""
+    return _solve("ipi_solve", h, o, device, v_out, pi_out)
+
+
+def vi_solve(h, o=None, device=False, v_out=None, pi_out=None):
+    return _solve("vi_solve", h, o, device, v_out, pi_out)
+
+
+def pi_solve(h, o=None, device=False, v_out=None, pi_out=None):
+    return _solve("pi_solve", h, o, device, v_out, pi_out)
+
+
+def opi_solve(h, o=None, device=False, v_out=None, pi_out=None):
+    return _solve("opi_solve", h, o, device, v_out, pi_out)
+
+
+def from_synth(m, device: bool = False) -> MDPHandle:
+    """Create a handle from an object with the fields of mdp_synth.SynthMDP."""
+    mask = None if m.mask is None else np.ascontiguousarray(m.mask, dtype=np.uint8)
+    g = np.ascontiguousarray(m.g, dtype=np.float64)
+    if device:
+        import torch
+        cv = lambda x: None if x is None else torch.from_numpy(np.ascontiguousarray(x)).cuda()
+        if m.kind == "dense":
+            return mdp_create_dense(cv(m.P), cv(g), m.gamma, cv(mask))
+        return mdp_create_ell(cv(m.col), cv(m.val), cv(g), m.gamma, cv(mask))
+    if m.kind == "dense":
+        return mdp_create_dense(np.ascontiguousarray(m.P), g, m.gamma, mask)
+    return mdp_create_ell(np.ascontiguousarray(m.col, dtype=np.int32),
+                          np.ascontiguousarray(m.val), g, m.gamma, mask)

@@ -1,0 +1,785 @@
+// C ABI of libmdpgpu: handle management, validation and the host drivers of the solvers.
+// Every arithmetic step runs in the kernels of sweep.cu and krylov.cu; the host only
+// enqueues launches and reads back the scalars that decide control flow.
+#include "mdp_internal.cuh"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+using namespace mdp;
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define CK(x)                                                                          \
+  do {                                                                                 \
+    cudaError_t e_ = (x);                                                              \
+    if (e_ != cudaSuccess) return fail(MDP_EDEVICE, std::string(#x) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+#define RK(x)                                                                          \
+  do {                                                                                 \
+    int r_ = (x);                                                                      \
+    if (r_ != MDP_OK) {                                                                \
+      if (r_ == MDP_EDEVICE) return fail(r_, std::string(#x) + ": " + cudaGetErrorString(cudaGetLastError())); \
+      if (g_err.empty()) g_err = #x;                                                   \
+      return r_;                                                                       \
+    }                                                                                  \
+  } while (0)
+
+inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct HostCtl {  // leading fields of GmresCtl read back by the host
+  int mode, status, i, W, steps, max_steps, restarts, dsel, from_rhs, est_runs, checks, pad_;
+};
+
+struct Workspace {
+  int kt = -1;
+  int W = 0;
+  int64_t ldq = 0;
+  void* Q = nullptr;
+  void* w0 = nullptr;
+  void* w1 = nullptr;
+  void* rbuf = nullptr;
+  void* d0 = nullptr;
+  void* d1 = nullptr;
+  void* phi = nullptr;
+  void* v = nullptr;   // value vector (double or float2)
+  void* tv = nullptr;
+  double* stage64 = nullptr;
+  int32_t* pi = nullptr;
+  int32_t* pi2 = nullptr;
+  GmresCtl* ctl = nullptr;
+  SweepOut* sout = nullptr;  // [4]
+  void* partials = nullptr;
+  unsigned* counter = nullptr;
+  int* flags = nullptr;
+  SweepOut* h_sout = nullptr;  // pinned
+  HostCtl* h_ctl = nullptr;    // pinned
+  size_t bytes = 0;
+};
+
+}  // namespace
+
+struct mdp_s {
+  DevMDP d{};
+  void* P = nullptr;
+  int32_t* col = nullptr;
+  double* g64 = nullptr;
+  float2* gdf = nullptr;
+  uint8_t* mask = nullptr;
+  double* gstage = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t own = nullptr;
+  int device = 0;
+  int timing = 0;
+  size_t data_bytes = 0;
+  Workspace ws;
+  std::vector<cudaEvent_t> ev;   // event pool (pairs)
+  std::vector<int> ev_kind;      // 0 sweep, 1 matvec
+  size_t ev_used = 0;
+  int launches = 0;
+};
+
+namespace {
+
+void free_ws(Workspace& w) {
+  void* ptrs[] = {w.Q, w.w0, w.w1, w.rbuf, w.d0, w.d1, w.phi, w.v, w.tv, w.stage64, w.pi, w.pi2,
+                  w.ctl, w.sout, w.partials, w.counter, w.flags};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (w.h_sout) cudaFreeHost(w.h_sout);
+  if (w.h_ctl) cudaFreeHost(w.h_ctl);
+  w = Workspace{};
+}
+
+int alloc0(void** p, size_t bytes, size_t& acc) {
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(MDP_ENOMEM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  acc += bytes;
+  if (cudaMemset(*p, 0, bytes) != cudaSuccess) return fail(MDP_EDEVICE, "cudaMemset failed");
+  return MDP_OK;
+}
+
+// kt: 0 double Krylov / double values, 1 float Krylov / double-float values
+int ensure_ws(mdp_t h, int kt, int W) {
+  Workspace& w = h->ws;
+  if (w.kt == kt && w.W >= W && w.ctl) return MDP_OK;
+  if (w.ctl) CK(cudaStreamSynchronize(h->stream));
+  free_ws(w);
+  const int64_t S = h->d.S;
+  w.kt = kt;
+  w.W = W;
+  w.ldq = round_up(std::max<int64_t>(S, h->d.ld), 32);
+  const size_t ek = kt ? 4 : 8;
+  const size_t vec = (size_t)w.ldq * ek;
+  size_t& acc = w.bytes;
+  RK(alloc0(&w.Q, vec * (W + 1), acc));
+  RK(alloc0(&w.w0, vec, acc));
+  RK(alloc0(&w.w1, vec, acc));
+  RK(alloc0(&w.rbuf, vec, acc));
+  RK(alloc0(&w.d0, vec, acc));
+  RK(alloc0(&w.d1, vec, acc));
+  RK(alloc0(&w.phi, vec, acc));
+  RK(alloc0(&w.v, (size_t)w.ldq * 8, acc));
+  RK(alloc0(&w.tv, (size_t)w.ldq * 8, acc));
+  RK(alloc0((void**)&w.stage64, (size_t)w.ldq * 8, acc));
+  RK(alloc0((void**)&w.pi, (size_t)w.ldq * 4, acc));
+  RK(alloc0((void**)&w.pi2, (size_t)w.ldq * 4, acc));
+  RK(alloc0((void**)&w.ctl, sizeof(GmresCtl), acc));
+  RK(alloc0((void**)&w.sout, 4 * sizeof(SweepOut), acc));
+  RK(alloc0(&w.partials, (size_t)MAX_RED_BLOCKS * (WMAX + 1) * 8, acc));
+  RK(alloc0((void**)&w.counter, 64, acc));
+  RK(alloc0((void**)&w.flags, 64, acc));
+  CK(cudaMallocHost((void**)&w.h_sout, 4 * sizeof(SweepOut)));
+  CK(cudaMallocHost((void**)&w.h_ctl, sizeof(HostCtl)));
+  return MDP_OK;
+}
+
+int krylov_grid(mdp_t h) {
+  const int64_t S = h->d.S;
+  int64_t g = (S + 1023) / 1024;
+  g = std::min<int64_t>(g, (int64_t)num_sms() * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, MAX_RED_BLOCKS));
+}
+
+KrylovBufs kbufs(mdp_t h) {
+  Workspace& w = h->ws;
+  KrylovBufs B;
+  B.kt = w.kt;
+  B.S = h->d.S;
+  B.ldq = w.ldq;
+  B.Q = w.Q;
+  B.w0 = w.w0;
+  B.w1 = w.w1;
+  B.rbuf = w.rbuf;
+  B.d0 = w.d0;
+  B.d1 = w.d1;
+  B.partials = w.partials;
+  B.counter = w.counter;
+  B.ctl = w.ctl;
+  B.grid = krylov_grid(h);
+  return B;
+}
+
+// ---------------------------------------------------------------- event timing
+int tic(mdp_t h, int kind) {
+  if (!h->timing) return -1;
+  if (h->ev_used + 2 > h->ev.size()) {
+    for (int i = 0; i < 256; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) return -1;
+      h->ev.push_back(e);
+    }
+    h->ev_kind.resize(h->ev.size() / 2 + 1);
+  }
+  int idx = (int)h->ev_used;
+  h->ev_used += 2;
+  h->ev_kind[idx / 2] = kind;
+  cudaEventRecord(h->ev[idx], h->stream);
+  return idx;
+}
+void toc(mdp_t h, int idx) {
+  if (idx >= 0) cudaEventRecord(h->ev[idx + 1], h->stream);
+}
+void collect_times(mdp_t h, mdp_stats* st) {
+  if (!h->timing) return;
+  for (size_t i = 0; i + 1 < h->ev_used; i += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->ev[i], h->ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      continue;
+    }
+    if (st) {
+      if (h->ev_kind[i / 2] == 0) { st->sweep_ms += ms; st->timed_sweeps += 1; }
+      else { st->matvec_ms += ms; st->timed_matvecs += 1; }
+    }
+  }
+  h->ev_used = 0;
+}
+
+// ---------------------------------------------------------------- algorithmic bytes
+double sweep_bytes(mdp_t h, bool policy_only, int arith) {
+  const DevMDP& d = h->d;
+  const double eb = d.pdt == MDP_F32 ? 4.0 : 8.0;
+  const double rows = policy_only ? (double)d.S : (double)d.S * d.A;
+  double b = d.kind == KIND_DENSE ? rows * (double)d.S * eb : rows * (double)d.k * (eb + 4.0);
+  b += rows * (arith ? 8.0 : 8.0);         // g (double or double-float)
+  b += (double)d.S * 8.0;                  // v
+  b += (double)d.S * (4.0 + 8.0 + (arith ? 4.0 : 8.0));  // pi, Tv, Phi writes
+  return b;
+}
+double matvec_bytes(mdp_t h, int kt) {
+  const DevMDP& d = h->d;
+  const double eb = d.pdt == MDP_F32 ? 4.0 : 8.0;
+  const double ek = kt ? 4.0 : 8.0;
+  double b = d.kind == KIND_DENSE ? (double)d.S * d.S * eb : (double)d.S * d.k * (eb + 4.0);
+  return b + (double)d.S * (4.0 + 3.0 * ek);
+}
+
+// ---------------------------------------------------------------- launch helpers
+int sweep(mdp_t h, int arith, const void* v, const int32_t* pi_in, int32_t* pi_out, void* tv_out,
+          double* tv64_out, void* phi_out, double* margin_out, SweepOut* out, mdp_stats* st) {
+  SweepLaunch L{};
+  L.d = h->d;
+  L.arith = arith;
+  L.v = v;
+  L.pi_in = pi_in;
+  L.pi_out = pi_out;
+  L.tv_out = tv_out;
+  L.tv64_out = tv64_out;
+  L.phi_out = phi_out;
+  L.margin_out = margin_out;
+  L.out = out;
+  L.partials = h->ws.partials;
+  L.counter = h->ws.counter;
+  int t = tic(h, pi_in ? 1 : 0);
+  int r = launch_sweep(L, h->stream);
+  toc(h, t);
+  h->launches += 1;
+  if (st) {
+    if (pi_in) st->matvecs += 1; else st->sweeps += 1;
+    st->bytes += sweep_bytes(h, pi_in != nullptr, arith);
+  }
+  return r == MDP_EDEVICE ? fail(r, std::string("sweep launch: ") + cudaGetErrorString(cudaGetLastError())) : r;
+}
+
+int read_sout(mdp_t h, int slot, SweepOut* out) {
+  CK(cudaMemcpyAsync(h->ws.h_sout + slot, h->ws.sout + slot, sizeof(SweepOut),
+                     cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *out = h->ws.h_sout[slot];
+  return MDP_OK;
+}
+
+int read_ctl(mdp_t h, HostCtl* c) {
+  CK(cudaMemcpyAsync(h->ws.h_ctl, h->ws.ctl, sizeof(HostCtl), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  *c = *h->ws.h_ctl;
+  return MDP_OK;
+}
+
+// Load an initial value vector (double, host or device; null = 0) into the workspace.
+int load_v(mdp_t h, const double* v0, int arith) {
+  Workspace& w = h->ws;
+  const int64_t S = h->d.S;
+  CK(cudaMemsetAsync(w.v, 0, (size_t)w.ldq * 8, h->stream));
+  if (!v0) return MDP_OK;
+  if (arith) {
+    CK(cudaMemcpyAsync(w.stage64, v0, (size_t)S * 8, cudaMemcpyDefault, h->stream));
+    RK(launch_d_to_df(w.stage64, (float2*)w.v, S, h->stream));
+  } else {
+    CK(cudaMemcpyAsync(w.v, v0, (size_t)S * 8, cudaMemcpyDefault, h->stream));
+  }
+  return MDP_OK;
+}
+
+int store_v(mdp_t h, const void* src, double* dst, int arith) {
+  const int64_t S = h->d.S;
+  if (arith) {
+    RK(launch_df_to_d((const float2*)src, h->ws.stage64, S, h->stream));
+    CK(cudaMemcpyAsync(dst, h->ws.stage64, (size_t)S * 8, cudaMemcpyDefault, h->stream));
+  } else {
+    CK(cudaMemcpyAsync(dst, src, (size_t)S * 8, cudaMemcpyDefault, h->stream));
+  }
+  return MDP_OK;
+}
+
+// One inner solve (Alg. 2 inner loop) on J^pi delta = rhs (rhs already in ws.phi, its norms
+// in ws.sout[slot]), with pi in ws.pi (or pi_dev).  thr: absolute target when alpha == 0.
+// On return delta is added to ws.v.
+int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double thr, int W,
+                int max_steps, mdp_stats* st, int* status_out) {
+  Workspace& w = h->ws;
+  const int kt = w.kt;
+  const int64_t S = h->d.S;
+  const size_t ek = kt ? 4 : 8;
+  KrylovBufs B = kbufs(h);
+  CK(cudaMemcpyAsync(w.rbuf, w.phi, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemsetAsync(w.d0, 0, (size_t)S * ek, h->stream));
+  RK(launch_gmres_init(B, thr, std::sqrt((double)S), W, max_steps, w.sout + slot, alpha,
+                       h->stream));
+  h->launches += 1;
+  MatvecLaunch M{};
+  M.d = h->d;
+  M.kt = kt;
+  M.pi = pi_dev;
+  M.ctl = w.ctl;
+  M.gate_mode = GM_STEP;
+  M.gate_mode2 = GM_STEP;
+  M.x_rhs = w.rbuf;
+  M.x_w0 = w.w0;
+  M.x_w1 = w.w1;
+  M.qbase = w.Q;
+  M.ldq = w.ldq;
+  M.a = 1.0;
+  M.b = 0.0;
+  M.c = -h->d.gamma;
+  M.out0 = w.w0;
+  M.out1 = w.w1;
+  M.partials = w.partials;
+  M.counter = w.counter;
+  MatvecLaunch C = M;  // true-residual check: r = rhs - J cand
+  C.gate_mode = GM_CHECK;
+  C.gate_mode2 = GM_RESTART;
+  C.ctl = nullptr;
+  C.ctl_rw = w.ctl;
+  C.x_w0 = w.d0;
+  C.x_w1 = w.d1;
+  C.a = -1.0;
+  C.b = 1.0;
+  C.c = h->d.gamma;
+  C.u = w.phi;
+  C.out = w.rbuf;
+  C.qbase = nullptr;
+  HostCtl hc{};
+  RK(read_ctl(h, &hc));
+  for (int it = 0; it <= max_steps + 1 && hc.mode != GM_DONE; ++it) {
+    int t = tic(h, 1);
+    RK(launch_matvec(M, h->stream));
+    toc(h, t);
+    RK(launch_cgs2_givens(B, h->stream));
+    RK(launch_estimate(B, h->stream));
+    RK(launch_candidate(B, h->stream));
+    RK(launch_matvec(C, h->stream));
+    h->launches += 7;
+    RK(read_ctl(h, &hc));
+  }
+  if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES did not reach a final state");
+  RK(launch_value_update(kt, w.v, w.d0, w.d1, w.ctl, nullptr, S, h->stream));
+  h->launches += 1;
+  if (st) {
+    st->inner += hc.steps;
+    st->restarts += hc.restarts;
+    st->matvecs += hc.steps + hc.checks;
+    const double ek2 = (double)ek;
+    st->bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, kt);
+    // CGS2: three passes over Q_0..Q_i plus w traffic, per step (i averaged over the cycle)
+    const double avg_m = std::min<double>(W, hc.steps) * 0.5 + 1.0;
+    st->bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * ek2;
+  }
+  if (status_out) *status_out = hc.status;
+  return MDP_OK;
+}
+
+mdp_opts normalise(const mdp_opts* o) {
+  mdp_opts r = o ? *o : mdp_opts_default();
+  return r;
+}
+
+int check_opts(mdp_t h, const mdp_opts& o) {
+  if (!h) return fail(MDP_EINVAL, "null handle");
+  if (o.restart < 1 || o.restart > WMAX) return fail(MDP_EINVAL, "restart must be in 1..64");
+  if (!(o.alpha >= 0.0 && o.alpha < 1.0)) return fail(MDP_EINVAL, "alpha must be in [0, 1)");
+  if (!(o.tol >= 0.0)) return fail(MDP_EINVAL, "tol must be >= 0");
+  if (o.max_outer < 0 || o.max_inner < 1) return fail(MDP_EINVAL, "bad iteration caps");
+  if (o.precision != MDP_PREC_FP64 && o.precision != MDP_PREC_MIXED)
+    return fail(MDP_EINVAL, "unknown precision");
+  if (o.precision == MDP_PREC_MIXED && h->d.pdt != MDP_F32)
+    return fail(MDP_EINVAL, "mixed precision needs FP32 transition data");
+  return MDP_OK;
+}
+
+double now_s() {
+  using namespace std::chrono;
+  return duration<double>(steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------- solvers (device buffers)
+enum Method { METH_IPI = 0, METH_VI = 1, METH_PI = 2, METH_OPI = 3 };
+
+// Policy evaluation to an absolute target by repeated inner solves on the current residual
+// (one solve in FP64; in FP32 Krylov each solve cuts the residual by up to 1e-5 and the
+// next residual is recomputed in double-float).
+int eval_policy(mdp_t h, const int32_t* pi_dev, int arith, double target, const mdp_opts& o,
+                mdp_stats* st, double* final_res) {
+  Workspace& w = h->ws;
+  const double floor_rel = arith ? 1e-5 : 0.0;
+  double res = INFINITY, prev = INFINITY;
+  for (int rep = 0; rep < 50; ++rep) {
+    // residual of pi at v: T^pi v - v (into phi) and its norms
+    RK(sweep(h, arith, w.v, pi_dev, nullptr, nullptr, nullptr, w.phi, nullptr, w.sout + 1, st));
+    SweepOut so;
+    RK(read_sout(h, 1, &so));
+    res = so.res_inf;
+    if (!(res > target)) break;
+    if (rep > 0 && !(res < 0.5 * prev)) break;  // stagnated at the arithmetic's floor
+    prev = res;
+    const double thr = std::max(target, floor_rel * res);
+    int status = 0;
+    RK(inner_gmres(h, pi_dev, 1, 0.0, thr, o.restart, o.max_inner, st, &status));
+    if (status == GS_CAP && !arith) break;
+  }
+  if (final_res) *final_res = res;
+  return MDP_OK;
+}
+
+int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* pi_out,
+               mdp_stats* st_user) {
+  const double t0 = now_s();
+  mdp_stats st{};
+  h->launches = 0;
+  const int arith = o.precision == MDP_PREC_MIXED ? 1 : 0;
+  RK(ensure_ws(h, arith, o.restart));
+  Workspace& w = h->ws;
+  RK(load_v(h, o.v0, arith));
+  int status = MDP_ENOCONV;
+  SweepOut so{};
+  int k = 0;
+  for (k = 0; k <= o.max_outer; ++k) {
+    // pi_k = GreedyPolicy(V_k), T V_k, Phi_k = T V_k - V_k and ||Phi_k||_inf
+    RK(sweep(h, arith, w.v, nullptr, w.pi, w.tv, nullptr, w.phi, nullptr, w.sout, &st));
+    RK(read_sout(h, 0, &so));
+    if (so.res_inf <= o.tol) { status = MDP_OK; break; }
+    if (k == o.max_outer) break;
+    if (method == METH_VI) {
+      std::swap(w.v, w.tv);
+    } else if (method == METH_OPI) {
+      std::swap(w.v, w.tv);  // first application of T^{pi_k} is T V_k
+      for (int j = 1; j < o.opi_W; ++j) {
+        RK(sweep(h, arith, w.v, w.pi, nullptr, w.tv, nullptr, nullptr, nullptr, w.sout + 2, &st));
+        std::swap(w.v, w.tv);
+      }
+    } else if (method == METH_IPI) {
+      int gs = 0;
+      RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, &st, &gs));
+    } else {  // PI: evaluate pi_k "exactly" (relative 10^-x of ||Phi_k||)
+      const double target = so.res_inf * std::pow(10.0, -(double)o.pi_inner_tol_exp);
+      double r = 0;
+      RK(eval_policy(h, w.pi, arith, target, o, &st, &r));
+    }
+  }
+  st.outer = k;
+  st.residual_inf = so.res_inf;
+  // v = T(V_K) of the last sweep, pi = GreedyPolicy(V_K)
+  RK(store_v(h, w.tv, v_out, arith));
+  if (pi_out) CK(cudaMemcpyAsync(pi_out, w.pi, (size_t)h->d.S * 4, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  collect_times(h, &st);
+  st.status = status;
+  st.launches = h->launches;
+  st.seconds = now_s() - t0;
+  if (st_user) *st_user = st;
+  if (status != MDP_OK) g_err = "iteration cap reached before ||T(v)-v||_inf <= tol";
+  return status;
+}
+
+// ---------------------------------------------------------------- creation
+int validate_args(int64_t S, int32_t A, int32_t k, int kind, int dt, double gamma,
+                  const void* P, const int32_t* col, const double* g) {
+  if (S < 1 || S > (int64_t)INT32_MAX - 64) return fail(MDP_EINVAL, "S must be in 1..2^31-65");
+  if (A < 1) return fail(MDP_EINVAL, "A must be >= 1");
+  if (kind == KIND_ELL && (k < 1 || (int64_t)k > S)) return fail(MDP_EINVAL, "k must be in 1..S");
+  if (dt != MDP_F32 && dt != MDP_F64) return fail(MDP_EINVAL, "dtype must be MDP_F32 or MDP_F64");
+  if (!(gamma > 0.0 && gamma < 1.0)) return fail(MDP_EINVAL, "gamma must be in (0, 1)");
+  if (!P || !g || (kind == KIND_ELL && !col)) return fail(MDP_EINVAL, "null input array");
+  return MDP_OK;
+}
+
+int upload_data(mdp_t h, const void* P, const int32_t* col, const double* g, const uint8_t* mask) {
+  DevMDP& d = h->d;
+  const size_t eb = d.pdt == MDP_F32 ? 4 : 8;
+  cudaStream_t s = h->stream;
+  if (d.kind == KIND_DENSE) {
+    CK(cudaMemsetAsync(h->P, 0, (size_t)d.S * d.A * d.ld * eb, s));
+    for (int a = 0; a < d.A; ++a) {
+      const char* src = (const char*)P + (size_t)a * d.S * d.S * eb;
+      char* dst = (char*)h->P + (size_t)a * d.ld * eb;
+      CK(cudaMemcpy2DAsync(dst, (size_t)d.A * d.ld * eb, src, (size_t)d.S * eb, (size_t)d.S * eb,
+                           (size_t)d.S, cudaMemcpyDefault, s));
+    }
+  } else {
+    CK(cudaMemsetAsync(h->P, 0, (size_t)d.S * d.A * d.kp * eb, s));
+    CK(cudaMemsetAsync(h->col, 0, (size_t)d.S * d.A * d.kp * 4, s));
+    for (int a = 0; a < d.A; ++a) {
+      const char* src = (const char*)P + (size_t)a * d.S * d.k * eb;
+      char* dst = (char*)h->P + (size_t)a * d.kp * eb;
+      CK(cudaMemcpy2DAsync(dst, (size_t)d.A * d.kp * eb, src, (size_t)d.k * eb, (size_t)d.k * eb,
+                           (size_t)d.S, cudaMemcpyDefault, s));
+      const char* srcc = (const char*)col + (size_t)a * d.S * d.k * 4;
+      char* dstc = (char*)h->col + (size_t)a * d.kp * 4;
+      CK(cudaMemcpy2DAsync(dstc, (size_t)d.A * d.kp * 4, srcc, (size_t)d.k * 4, (size_t)d.k * 4,
+                           (size_t)d.S, cudaMemcpyDefault, s));
+    }
+  }
+  CK(cudaMemcpyAsync(h->gstage, g, (size_t)d.S * d.A * 8, cudaMemcpyDefault, s));
+  RK(launch_cost_transpose(h->gstage, h->g64, h->gdf, d.S, d.A, s));
+  if (mask) CK(cudaMemcpyAsync(h->mask, mask, (size_t)d.S * d.A, cudaMemcpyDefault, s));
+  // validate on the device
+  int* flags = nullptr;
+  CK(cudaMalloc((void**)&flags, 8 * sizeof(int)));
+  cudaMemsetAsync(flags, 0, 8 * sizeof(int), s);
+  int r = launch_validate(d, flags, s);
+  int hf[8] = {0};
+  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamSynchronize(s);
+  cudaFree(flags);
+  if (r != MDP_OK || e != cudaSuccess) return fail(MDP_EDEVICE, std::string("validation: ") + cudaGetErrorString(e));
+  if (hf[0]) return fail(MDP_EINVAL, "transition probabilities must be finite and >= 0");
+  if (hf[1]) return fail(MDP_EINVAL, "ELL column index out of range [0, S)");
+  if (hf[2]) return fail(MDP_EINVAL, "a transition row does not sum to 1 within tolerance");
+  if (hf[3]) return fail(MDP_EINVAL, "costs must be finite");
+  if (hf[4]) return fail(MDP_EINVAL, "every state needs at least one allowed action");
+  return MDP_OK;
+}
+
+int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int dt,
+                  const int32_t* col, const double* g, double gamma, const uint8_t* mask,
+                  mdp_t* out) {
+  g_err.clear();
+  if (!out) return fail(MDP_EINVAL, "null output handle pointer");
+  *out = nullptr;
+  RK(validate_args(S, A, k, kind, dt, gamma, P, col, g));
+  mdp_t h = new (std::nothrow) mdp_s();
+  if (!h) return fail(MDP_ENOMEM, "host allocation failed");
+  cudaGetDevice(&h->device);
+  if (cudaStreamCreateWithFlags(&h->own, cudaStreamNonBlocking) != cudaSuccess) {
+    delete h;
+    return fail(MDP_EDEVICE, "cudaStreamCreate failed");
+  }
+  h->stream = h->own;
+  DevMDP& d = h->d;
+  d.S = S;
+  d.A = A;
+  d.k = kind == KIND_ELL ? k : (int32_t)std::min<int64_t>(S, INT32_MAX);
+  d.kp = kind == KIND_ELL ? (int32_t)round_up(k, 4) : 0;
+  d.ld = kind == KIND_DENSE ? round_up(S, 4) : 0;
+  d.kind = kind;
+  d.pdt = dt;
+  d.gamma = gamma;
+  d.gamma_hi = (float)gamma;
+  d.gamma_lo = (float)(gamma - (double)d.gamma_hi);
+  const size_t eb = dt == MDP_F32 ? 4 : 8;
+  size_t acc = 0;
+  int r = MDP_OK;
+  auto bail = [&](int code) {
+    mdp_destroy(h);
+    return code;
+  };
+  if (kind == KIND_DENSE) r = alloc0(&h->P, (size_t)S * A * d.ld * eb, acc);
+  else {
+    r = alloc0(&h->P, (size_t)S * A * d.kp * eb, acc);
+    if (r == MDP_OK) r = alloc0((void**)&h->col, (size_t)S * A * d.kp * 4, acc);
+  }
+  if (r == MDP_OK) r = alloc0((void**)&h->g64, (size_t)S * A * 8, acc);
+  if (r == MDP_OK && dt == MDP_F32) r = alloc0((void**)&h->gdf, (size_t)S * A * 8, acc);
+  if (r == MDP_OK) r = alloc0((void**)&h->gstage, (size_t)S * A * 8, acc);
+  if (r == MDP_OK && mask) r = alloc0((void**)&h->mask, (size_t)S * A, acc);
+  if (r != MDP_OK) return bail(r);
+  h->data_bytes = acc;
+  d.P = h->P;
+  d.col = h->col;
+  d.g64 = h->g64;
+  d.gdf = h->gdf;
+  d.mask = h->mask;
+  r = upload_data(h, P, col, g, mask);
+  if (r != MDP_OK) return bail(r);
+  *out = h;
+  return MDP_OK;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+mdp_opts mdp_opts_default(void) {
+  mdp_opts o;
+  o.alpha = 0.1;
+  o.tol = 1e-8;
+  o.restart = 30;
+  o.max_outer = 100;
+  o.max_inner = 3000;
+  o.precision = MDP_PREC_MIXED;
+  o.opi_W = 50;
+  o.pi_inner_tol_exp = 13;
+  o.v0 = nullptr;
+  return o;
+}
+
+const char* mdp_last_error(void) { return g_err.c_str(); }
+const char* mdp_version(void) { return "mdpgpu 0.1 (sm_103a)"; }
+
+int mdp_create_dense(int64_t S, int32_t A, const void* P, int p_dtype, const double* g,
+                     double gamma, const uint8_t* mask, mdp_t* out) {
+  return create_common(S, A, 0, KIND_DENSE, P, p_dtype, nullptr, g, gamma, mask, out);
+}
+int mdp_create_ell(int64_t S, int32_t A, int32_t k, const int32_t* col, const void* val,
+                   int val_dtype, const double* g, double gamma, const uint8_t* mask,
+                   mdp_t* out) {
+  return create_common(S, A, k, KIND_ELL, val, val_dtype, col, g, gamma, mask, out);
+}
+int mdp_create_dense_dev(int64_t S, int32_t A, const void* P, int p_dtype, const double* g,
+                         double gamma, const uint8_t* mask, mdp_t* out) {
+  return create_common(S, A, 0, KIND_DENSE, P, p_dtype, nullptr, g, gamma, mask, out);
+}
+int mdp_create_ell_dev(int64_t S, int32_t A, int32_t k, const int32_t* col, const void* val,
+                       int val_dtype, const double* g, double gamma, const uint8_t* mask,
+                       mdp_t* out) {
+  return create_common(S, A, k, KIND_ELL, val, val_dtype, col, g, gamma, mask, out);
+}
+
+int mdp_load_dense(mdp_t h, const void* P, const double* g) {
+  g_err.clear();
+  if (!h || h->d.kind != KIND_DENSE || !P || !g) return fail(MDP_EINVAL, "bad handle or input");
+  return upload_data(h, P, nullptr, g, nullptr);
+}
+int mdp_load_ell(mdp_t h, const int32_t* col, const void* val, const double* g) {
+  g_err.clear();
+  if (!h || h->d.kind != KIND_ELL || !col || !val || !g) return fail(MDP_EINVAL, "bad handle or input");
+  return upload_data(h, val, col, g, nullptr);
+}
+
+void mdp_destroy(mdp_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  free_ws(h->ws);
+  void* ptrs[] = {h->P, h->col, h->g64, h->gdf, h->mask, h->gstage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->own) cudaStreamDestroy(h->own);
+  delete h;
+}
+
+int mdp_set_stream(mdp_t h, void* stream) {
+  if (!h) return fail(MDP_EINVAL, "null handle");
+  CK(cudaStreamSynchronize(h->stream));
+  h->stream = stream ? (cudaStream_t)stream : h->own;
+  return MDP_OK;
+}
+
+int mdp_set_timing(mdp_t h, int on) {
+  if (!h) return fail(MDP_EINVAL, "null handle");
+  h->timing = on ? 1 : 0;
+  return MDP_OK;
+}
+
+int mdp_info(mdp_t h, int64_t* S, int32_t* A, int32_t* k, int32_t* kind, int32_t* dtype,
+             double* gamma) {
+  if (!h) return fail(MDP_EINVAL, "null handle");
+  if (S) *S = h->d.S;
+  if (A) *A = h->d.A;
+  if (k) *k = h->d.kind == KIND_ELL ? h->d.k : 0;
+  if (kind) *kind = h->d.kind;
+  if (dtype) *dtype = h->d.pdt;
+  if (gamma) *gamma = h->d.gamma;
+  return MDP_OK;
+}
+
+int64_t mdp_device_bytes(mdp_t h) {
+  if (!h) return -1;
+  return (int64_t)(h->data_bytes + h->ws.bytes);
+}
+
+int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double* margin,
+                      double* res_inf, int32_t precision) {
+  g_err.clear();
+  if (!h || !v) return fail(MDP_EINVAL, "null handle or v");
+  const int arith = precision == MDP_PREC_MIXED ? 1 : 0;
+  if (arith && h->d.pdt != MDP_F32) return fail(MDP_EINVAL, "mixed precision needs FP32 data");
+  RK(ensure_ws(h, arith, h->ws.W > 0 ? h->ws.W : 30));
+  RK(load_v(h, v, arith));
+  RK(sweep(h, arith, h->ws.v, nullptr, pi, nullptr, Tv, nullptr, margin, h->ws.sout, nullptr));
+  if (res_inf) {
+    SweepOut so;
+    RK(read_sout(h, 0, &so));
+    *res_inf = so.res_inf;
+  }
+  return MDP_OK;
+}
+
+int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res_inf,
+                  int32_t precision) {
+  g_err.clear();
+  if (!h || !v) return fail(MDP_EINVAL, "null handle or v");
+  const int arith = precision == MDP_PREC_MIXED ? 1 : 0;
+  if (arith && h->d.pdt != MDP_F32) return fail(MDP_EINVAL, "mixed precision needs FP32 data");
+  RK(ensure_ws(h, arith, h->ws.W > 0 ? h->ws.W : 30));
+  Workspace& w = h->ws;
+  const int64_t S = h->d.S;
+  RK(load_v(h, v, arith));
+  RK(sweep(h, arith, w.v, nullptr, w.pi2, nullptr, w.stage64, nullptr, nullptr, w.sout, nullptr));
+  if (Tv) CK(cudaMemcpyAsync(Tv, w.stage64, (size_t)S * 8, cudaMemcpyDeviceToHost, h->stream));
+  if (pi) CK(cudaMemcpyAsync(pi, w.pi2, (size_t)S * 4, cudaMemcpyDeviceToHost, h->stream));
+  SweepOut so;
+  RK(read_sout(h, 0, &so));
+  if (res_inf) *res_inf = so.res_inf;
+  return MDP_OK;
+}
+
+int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double target_inf,
+                          const mdp_opts* opts, double* v_out, mdp_stats* stats) {
+  g_err.clear();
+  mdp_opts o = normalise(opts);
+  RK(check_opts(h, o));
+  if (!pi || !v_out) return fail(MDP_EINVAL, "null pi or v_out");
+  if (!(target_inf >= 0.0)) return fail(MDP_EINVAL, "target must be >= 0");
+  const double t0 = now_s();
+  mdp_stats st{};
+  h->launches = 0;
+  const int arith = o.precision == MDP_PREC_MIXED ? 1 : 0;
+  RK(ensure_ws(h, arith, o.restart));
+  Workspace& w = h->ws;
+  CK(cudaMemcpyAsync(w.pi2, pi, (size_t)h->d.S * 4, cudaMemcpyDefault, h->stream));
+  {
+    CK(cudaMemsetAsync(w.flags, 0, 64, h->stream));
+    RK(launch_check_policy(w.pi2, h->d.S, h->d.A, h->d.mask, w.flags, h->stream));
+    int hf[16] = {0};
+    CK(cudaMemcpyAsync(hf, w.flags, 64, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    if (hf[5]) return fail(MDP_EINVAL, "policy entry out of range or not an allowed action");
+  }
+  RK(load_v(h, v0, arith));
+  double res = 0;
+  RK(eval_policy(h, w.pi2, arith, target_inf, o, &st, &res));
+  RK(store_v(h, w.v, v_out, arith));
+  CK(cudaStreamSynchronize(h->stream));
+  collect_times(h, &st);
+  st.residual_inf = res;
+  st.status = res <= target_inf ? MDP_OK : MDP_ENOCONV;
+  st.launches = h->launches;
+  st.seconds = now_s() - t0;
+  if (stats) *stats = st;
+  if (st.status != MDP_OK) g_err = "policy evaluation did not reach the target";
+  return st.status;
+}
+
+int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double target_inf,
+                      const mdp_opts* opts, double* v_out, mdp_stats* stats) {
+  // host pointers: cudaMemcpyDefault handles them through the same path
+  return policy_eval_gmres_dev(h, pi, v0, target_inf, opts, v_out, stats);
+}
+
+#define SOLVER(name, method)                                                            \
+  int name##_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,         \
+                 mdp_stats* stats) {                                                    \
+    g_err.clear();                                                                      \
+    mdp_opts o = normalise(opts);                                                       \
+    RK(check_opts(h, o));                                                               \
+    if (!v_out) return fail(MDP_EINVAL, "null v_out");                                  \
+    if (method == METH_OPI && o.opi_W < 1) return fail(MDP_EINVAL, "opi_W must be >= 1");  \
+    return run_solver(h, method, o, v_out, pi_out, stats);                              \
+  }                                                                                     \
+  int name(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out, mdp_stats* stats) { \
+    return name##_dev(h, opts, v_out, pi_out, stats);                                   \
+  }
+
+SOLVER(ipi_solve, METH_IPI)
+SOLVER(vi_solve, METH_VI)
+SOLVER(pi_solve, METH_PI)
+SOLVER(opi_solve, METH_OPI)
+
+}  // extern "C"

@@ -1,0 +1,800 @@
+// Restarted GMRES(W) for the inexact policy evaluation of Alg. 2 (paper Sec. 2.2, 3.1):
+//
+//   P^pi matvec   w = J^pi q = q - gamma P^pi q, rows of P_{pi(s)} gathered on the fly
+//   Arnoldi       classical Gram-Schmidt with one re-orthogonalisation (CGS2), the Hessenberg
+//                 column H[0..i+1][i] in FP64
+//   least squares Givens rotations on H in FP64, |gv[i+1]| = ||beta e1 - H y||_2
+//   stopping rule ||g^pi - J^pi V||_inf <= thr, tested on the true residual; a cheap bound
+//                 from the Arnoldi relation decides when the true test is worth a matvec
+//
+// The inner solver is a device-resident state machine (GmresCtl.mode): every kernel of an
+// Arnoldi step checks the mode and returns at once when it is not due, and only the last
+// block of a grid (after all blocks have read the mode) changes it.
+#include "mdp_internal.cuh"
+
+#include <algorithm>
+#include <math.h>
+
+namespace mdp {
+
+namespace {
+
+template <class KT> __device__ __forceinline__ KT coef(const double* d, const float* f, int j);
+template <> __device__ __forceinline__ double coef<double>(const double* d, const float*, int j) {
+  return d[j];
+}
+template <> __device__ __forceinline__ float coef<float>(const double*, const float* f, int j) {
+  return f[j];
+}
+template <class KT> __device__ __forceinline__ KT scale_of(const GmresCtl* c);
+template <> __device__ __forceinline__ double scale_of<double>(const GmresCtl* c) { return c->xscale; }
+template <> __device__ __forceinline__ float scale_of<float>(const GmresCtl* c) { return c->xscalef; }
+
+__device__ __forceinline__ void set_scale(GmresCtl* c, double s) {
+  c->xscale = s;
+  c->xscalef = (float)s;
+}
+
+// Move to the next Arnoldi step of the cycle, or to a restart when the cycle is full.
+__device__ __forceinline__ void advance(GmresCtl* c) {
+  if (c->i >= c->W - 1) {
+    c->mode = GM_RESTART;
+  } else {
+    c->i += 1;
+    c->from_rhs = 0;
+    set_scale(c, 1.0 / c->hnext);
+    c->mode = GM_STEP;
+  }
+}
+
+// ------------------------------------------------------------------ P^pi matvec
+struct MatvecK {
+  DevMDP d;
+  const int32_t* pi;
+  const void* x;
+  GmresCtl* ctl;
+  int gate_mode, gate_mode2;
+  const void* x_rhs;
+  const void* x_w0;
+  const void* x_w1;
+  void* qbase;
+  int64_t ldq;
+  double a, b, c;
+  const void* u;
+  void* out;
+  void* out0;
+  void* out1;
+  SweepOut* norms;
+  int finalize_check;
+  void* partials;
+  unsigned* counter;
+};
+
+// Resolved per launch (uniform over the grid): input, its scale, output and side output.
+template <class KT> struct MvIO {
+  const KT* x;
+  KT scale;
+  KT* out;
+  KT* qside;
+  bool run;
+};
+
+template <class KT>
+__device__ __forceinline__ MvIO<KT> resolve(const MatvecK& p) {
+  MvIO<KT> io;
+  io.run = true;
+  io.x = (const KT*)p.x;
+  io.scale = KT(1);
+  io.out = (KT*)p.out;
+  io.qside = nullptr;
+  if (p.ctl) {
+    const GmresCtl* c = p.ctl;
+    int mode = *(volatile const int*)&c->mode;
+    io.run = (mode == p.gate_mode || mode == p.gate_mode2);
+    if (p.gate_mode == GM_STEP) {
+      const int i = c->i;
+      io.x = c->from_rhs ? (const KT*)p.x_rhs : (const KT*)((i - 1) & 1 ? p.x_w1 : p.x_w0);
+      io.scale = scale_of<KT>(c);
+      io.out = (KT*)((i & 1) ? p.out1 : p.out0);
+      io.qside = (KT*)p.qbase + (int64_t)i * p.ldq;
+    } else {
+      io.x = (const KT*)(c->dsel ? p.x_w0 : p.x_w1);  // candidate = dbuf[1 - dsel]
+    }
+  }
+  return io;
+}
+
+template <class KT>
+__device__ __forceinline__ void matvec_finish(const MatvecK& p, KT mx, KT ss) {
+  __shared__ KT shr[32];
+  KT bm = block_max(mx, shr);
+  KT bs = block_sum(ss, shr);
+  KT* part = (KT*)p.partials;
+  if (threadIdx.x == 0) {
+    part[2 * blockIdx.x] = bm;
+    part[2 * blockIdx.x + 1] = bs;
+  }
+  if (!arrive_last(p.counter)) return;
+  KT m = 0, t = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    m = max(m, __ldcg(part + 2 * b));
+    t += __ldcg(part + 2 * b + 1);
+  }
+  m = block_max(m, shr);
+  t = block_sum(t, shr);
+  if (threadIdx.x != 0) return;
+  const double rinf = (double)m, rn2 = sqrt((double)t);
+  if (p.norms) {
+    p.norms->res_inf = rinf;
+    p.norms->res_nrm2 = rn2;
+  }
+  if (!p.ctl) return;
+  GmresCtl* c = p.ctl;
+  if (p.gate_mode == GM_STEP) {
+    c->last_nrm2 = rn2;  // ||J q_i||_2 before orthogonalisation (breakdown reference)
+    return;
+  }
+  // true-residual check of the candidate (CHECK) or restart from it (RESTART)
+  c->checks += 1;
+  c->last_inf = rinf;
+  const int mode = c->mode;
+  if (rinf <= c->thr) {
+    c->mode = GM_DONE;
+    c->status = GS_CONVERGED;
+    c->dsel = 1 - c->dsel;  // the candidate becomes the result
+    return;
+  }
+  if (mode == GM_CHECK && c->i < c->W - 1) {
+    advance(c);
+    return;
+  }
+  // restart (Alg. 2: cycle full) from the candidate and its true residual (now in rbuf)
+  c->dsel = 1 - c->dsel;
+  c->restarts += 1;
+  c->beta = rn2;
+  for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
+  c->gv[0] = rn2;
+  c->i = 0;
+  c->from_rhs = 1;
+  set_scale(c, rn2 > 0.0 ? 1.0 / rn2 : 0.0);
+  c->mode = (rn2 > 0.0) ? GM_STEP : GM_DONE;
+  if (rn2 == 0.0) c->status = GS_CONVERGED;
+}
+
+template <class PT, class KT, int T>
+__global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
+  const MvIO<KT> io = resolve<KT>(p);
+  if (!io.run) return;
+  const DevMDP& d = p.d;
+  const int nteams = blockDim.x / T;
+  const int team = threadIdx.x / T, tl = threadIdx.x % T;
+  const PT* val = (const PT*)d.P;
+  const int nvec = d.kp >> 2;
+  const KT* u = (const KT*)p.u;
+  const KT ca = (KT)p.a, cb = (KT)p.b, cc = (KT)p.c;
+  KT mx = 0, ss = 0;
+  const int64_t nteam_total = (int64_t)gridDim.x * nteams;
+  for (int64_t sb = (int64_t)blockIdx.x * nteams; sb < d.S; sb += nteam_total) {
+    const int64_t s = sb + team;
+    const bool act = s < d.S;
+    KT acc = 0;
+    if (act) {
+      const int64_t base = ((int64_t)s * d.A + p.pi[s]) * d.kp;
+      for (int q = tl; q < nvec; q += T) {
+        float4 vv;
+        KT v0, v1, v2, v3;
+        if constexpr (sizeof(PT) == 4) {
+          vv = __ldcs(reinterpret_cast<const float4*>(val + base) + q);
+          v0 = (KT)vv.x; v1 = (KT)vv.y; v2 = (KT)vv.z; v3 = (KT)vv.w;
+        } else {
+          double2 t0 = __ldcs(reinterpret_cast<const double2*>(val + base + 4 * q));
+          double2 t1 = __ldcs(reinterpret_cast<const double2*>(val + base + 4 * q) + 1);
+          v0 = (KT)t0.x; v1 = (KT)t0.y; v2 = (KT)t1.x; v3 = (KT)t1.y;
+        }
+        int4 c4 = __ldcs(reinterpret_cast<const int4*>(d.col + base) + q);
+        acc = fma(v0, __ldg(io.x + c4.x), acc);
+        acc = fma(v1, __ldg(io.x + c4.y), acc);
+        acc = fma(v2, __ldg(io.x + c4.z), acc);
+        acc = fma(v3, __ldg(io.x + c4.w), acc);
+      }
+    }
+#pragma unroll
+    for (int o = T >> 1; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (act && tl == 0) {
+      const KT xs = io.x[s] * io.scale;
+      KT r = ca * xs + cc * (acc * io.scale);
+      if (u) r += cb * u[s];
+      io.out[s] = r;
+      if (io.qside) io.qside[s] = xs;
+      mx = max(mx, (KT)fabs(r));
+      ss += r * r;
+    }
+  }
+  matvec_finish<KT>(p, mx, ss);
+}
+
+template <class PT, class KT>
+__global__ void __launch_bounds__(256) matvec_dense_kernel(MatvecK p) {
+  const MvIO<KT> io = resolve<KT>(p);
+  if (!io.run) return;
+  const DevMDP& d = p.d;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const PT* P = (const PT*)d.P;
+  const KT* u = (const KT*)p.u;
+  const KT ca = (KT)p.a, cb = (KT)p.b, cc = (KT)p.c;
+  KT mx = 0, ss = 0;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < d.S; s += nw) {
+    const PT* row = P + ((int64_t)s * d.A + p.pi[s]) * d.ld;
+    KT acc0 = 0, acc1 = 0;
+    int64_t c = 4 * lane;
+    for (; c + 128 < d.ld; c += 256) {
+      KT xa[4], xb[4], pa[4], pb[4];
+      if constexpr (sizeof(KT) == 4) {
+        float4 t = __ldg(reinterpret_cast<const float4*>(io.x + c));
+        float4 t2 = __ldg(reinterpret_cast<const float4*>(io.x + c + 128));
+        xa[0] = t.x; xa[1] = t.y; xa[2] = t.z; xa[3] = t.w;
+        xb[0] = t2.x; xb[1] = t2.y; xb[2] = t2.z; xb[3] = t2.w;
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { xa[e] = __ldg(io.x + c + e); xb[e] = __ldg(io.x + c + 128 + e); }
+      }
+      if constexpr (sizeof(PT) == 4) {
+        float4 t = __ldcs(reinterpret_cast<const float4*>(row + c));
+        float4 t2 = __ldcs(reinterpret_cast<const float4*>(row + c + 128));
+        pa[0] = t.x; pa[1] = t.y; pa[2] = t.z; pa[3] = t.w;
+        pb[0] = t2.x; pb[1] = t2.y; pb[2] = t2.z; pb[3] = t2.w;
+      } else {
+        double2 t0 = __ldcs(reinterpret_cast<const double2*>(row + c));
+        double2 t1 = __ldcs(reinterpret_cast<const double2*>(row + c) + 1);
+        double2 t2 = __ldcs(reinterpret_cast<const double2*>(row + c + 128));
+        double2 t3 = __ldcs(reinterpret_cast<const double2*>(row + c + 128) + 1);
+        pa[0] = t0.x; pa[1] = t0.y; pa[2] = t1.x; pa[3] = t1.y;
+        pb[0] = t2.x; pb[1] = t2.y; pb[2] = t3.x; pb[3] = t3.y;
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) { acc0 = fma(pa[e], xa[e], acc0); acc1 = fma(pb[e], xb[e], acc1); }
+    }
+    for (; c < d.ld; c += 128) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc0 = fma((KT)row[c + e], __ldg(io.x + c + e), acc0);
+    }
+    KT acc = warp_sum(acc0 + acc1);
+    if (lane == 0) {
+      const KT xs = io.x[s] * io.scale;
+      KT r = ca * xs + cc * (acc * io.scale);
+      if (u) r += cb * u[s];
+      io.out[s] = r;
+      if (io.qside) io.qside[s] = xs;
+      mx = max(mx, (KT)fabs(r));
+      ss += r * r;
+    }
+  }
+  matvec_finish<KT>(p, mx, ss);
+}
+
+template <class Kern>
+int grid_for(Kern k, int threads, size_t smem, int64_t work_units) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess)
+    per_sm = 1;
+  per_sm = std::max(per_sm, 1);
+  int64_t g = (int64_t)num_sms() * per_sm;
+  g = std::min<int64_t>(g, std::max<int64_t>(work_units, 1));
+  g = std::min<int64_t>(g, MAX_RED_BLOCKS);
+  return (int)std::max<int64_t>(g, 1);
+}
+
+template <class PT, class KT>
+int launch_mv_typed(const MatvecLaunch& L, cudaStream_t st) {
+  MatvecK p{L.d, L.pi, L.x, L.ctl_rw ? L.ctl_rw : const_cast<GmresCtl*>(L.ctl),
+            L.gate_mode, L.gate_mode2, L.x_rhs, L.x_w0, L.x_w1, L.qbase, L.ldq,
+            L.a, L.b, L.c, L.u, L.out, L.out0, L.out1, L.norms, L.ctl_rw != nullptr,
+            L.partials, L.counter};
+  const DevMDP& d = L.d;
+  if (d.kind == KIND_DENSE) {
+    auto k = matvec_dense_kernel<PT, KT>;
+    int grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, (d.S + 7) / 8);
+    k<<<grid, 256, 0, st>>>(p);
+  } else {
+    int T = L.lanes;
+    if (T <= 0) T = (d.kp / 4 >= 8) ? 8 : ((d.kp / 4 >= 4) ? 4 : ((d.kp / 4 >= 2) ? 2 : 1));
+    const int64_t units = (d.S + 256 / T - 1) / (256 / T);
+    int grid = 1;
+    switch (T) {
+      case 1: { auto k = matvec_ell_kernel<PT, KT, 1>; grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units); k<<<grid, 256, 0, st>>>(p); break; }
+      case 2: { auto k = matvec_ell_kernel<PT, KT, 2>; grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units); k<<<grid, 256, 0, st>>>(p); break; }
+      case 4: { auto k = matvec_ell_kernel<PT, KT, 4>; grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units); k<<<grid, 256, 0, st>>>(p); break; }
+      case 8: { auto k = matvec_ell_kernel<PT, KT, 8>; grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units); k<<<grid, 256, 0, st>>>(p); break; }
+      default: return MDP_EINVAL;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+// ------------------------------------------------------------------ tall-skinny kernels
+struct KB {
+  int64_t S, ldq;
+  void* Q;
+  void* w0;
+  void* w1;
+  void* rbuf;
+  void* d0;
+  void* d1;
+  void* partials;
+  unsigned* counter;
+  GmresCtl* ctl;
+};
+
+__device__ __forceinline__ void block_rows(int64_t S, int64_t& r0, int64_t& r1) {
+  int64_t per = (S + gridDim.x - 1) / gridDim.x;
+  per = (per + 31) & ~int64_t(31);
+  r0 = (int64_t)blockIdx.x * per;
+  r1 = min(S, r0 + per);
+}
+
+// Per-block dot products Q_j^T w over the block's rows for j < m; warp w handles columns
+// j = w, w + 8, ...; result in part[blockIdx.x * (WMAX+1) + j].
+template <class KT>
+__device__ __forceinline__ void block_dots(const KT* Q, int64_t ldq, const KT* w, int m,
+                                           int64_t r0, int64_t r1, KT* part) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < m; j += nw) {
+    const KT* q = Q + (int64_t)j * ldq;
+    KT acc = 0;
+    for (int64_t r = r0 + lane; r < r1; r += 32) acc = fma(q[r], w[r], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) part[(int64_t)blockIdx.x * (WMAX + 1) + j] = acc;
+  }
+}
+
+// Last block: out[j] = sum over blocks of part[b][j], j < m.
+template <class KT>
+__device__ __forceinline__ void reduce_dots(const KT* part, int m, double* outd, float* outf) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = wid; j < m; j += nw) {
+    KT acc = 0;
+    for (int b = lane; b < (int)gridDim.x; b += 32) acc += __ldcg(part + (int64_t)b * (WMAX + 1) + j);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      outd[j] = (double)acc;
+      outf[j] = (float)acc;
+    }
+  }
+}
+
+template <class KT>
+__global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
+  GmresCtl* c = b.ctl;
+  if (*(volatile int*)&c->mode != GM_STEP) return;
+  const int i = c->i, m = i + 1;
+  const KT* w = (const KT*)((i & 1) ? b.w1 : b.w0);
+  int64_t r0, r1;
+  block_rows(b.S, r0, r1);
+  block_dots<KT>((const KT*)b.Q, b.ldq, w, m, r0, r1, (KT*)b.partials);
+  if (!arrive_last(b.counter)) return;
+  reduce_dots<KT>((const KT*)b.partials, m, c->c1, c->c1f);
+}
+
+template <class KT>
+__global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
+  GmresCtl* c = b.ctl;
+  if (*(volatile int*)&c->mode != GM_STEP) return;
+  const int i = c->i, m = i + 1;
+  KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
+  const KT* Q = (const KT*)b.Q;
+  int64_t r0, r1;
+  block_rows(b.S, r0, r1);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    KT x = w[r];
+    for (int j = 0; j < m; ++j) x = fma(-coef<KT>(c->c1, c->c1f, j), Q[(int64_t)j * b.ldq + r], x);
+    w[r] = x;
+  }
+  __syncthreads();
+  block_dots<KT>(Q, b.ldq, w, m, r0, r1, (KT*)b.partials);
+  if (!arrive_last(b.counter)) return;
+  reduce_dots<KT>((const KT*)b.partials, m, c->c2, c->c2f);
+}
+
+// Givens update of column i of H and the stopping/restart decision (thread 0, FP64).
+__device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
+  const int i = c->i;
+  double* Hc = c->H + (int64_t)(WMAX + 1) * i;
+  for (int j = 0; j <= i; ++j) Hc[j] = c->c1[j] + c->c2[j];
+  Hc[i + 1] = hnext;
+  c->hnext = hnext;
+  for (int j = 0; j < i; ++j) {
+    const double t = c->cs[j] * Hc[j] + c->sn[j] * Hc[j + 1];
+    Hc[j + 1] = -c->sn[j] * Hc[j] + c->cs[j] * Hc[j + 1];
+    Hc[j] = t;
+  }
+  const double a = Hc[i], bb = Hc[i + 1];
+  const double r = hypot(a, bb);
+  double cs = 1.0, sn = 0.0;
+  if (r > 0.0) { cs = a / r; sn = bb / r; }
+  c->cs[i] = cs;
+  c->sn[i] = sn;
+  Hc[i] = r;
+  Hc[i + 1] = 0.0;
+  c->gv[i + 1] = -sn * c->gv[i];
+  c->gv[i] = cs * c->gv[i];
+  c->rho = fabs(c->gv[i + 1]);
+  c->steps += 1;
+  // breakdown: the new direction vanished to working precision (reading of "||q||_2 = 0")
+  const double eps = fp32_basis ? 3.0e-6 : 1.0e-14;
+  const bool breakdown = !(hnext > eps * c->last_nrm2);
+  int mode;
+  if (breakdown) {
+    mode = GM_FINISH;
+    c->status = GS_BREAKDOWN;
+  } else if (c->steps >= c->max_steps) {
+    mode = GM_FINISH;
+    c->status = GS_CAP;
+  } else if (c->rho <= c->sqrtS * c->thr) {
+    mode = GM_EST;
+  } else if (i >= c->W - 1) {
+    mode = GM_RESTART;
+  } else {
+    mode = GM_STEP;
+  }
+  if (mode != GM_STEP) {
+    // y solves the (i+1)x(i+1) triangular system R y = gv[0..i]
+    for (int j = i; j >= 0; --j) {
+      double t = c->gv[j];
+      for (int l = j + 1; l <= i; ++l) t -= c->H[(int64_t)(WMAX + 1) * l + j] * c->y[l];
+      const double rjj = c->H[(int64_t)(WMAX + 1) * j + j];
+      c->y[j] = (rjj != 0.0) ? t / rjj : 0.0;
+      c->yf[j] = (float)c->y[j];
+    }
+  }
+  if (mode == GM_EST) {
+    // residual coefficients in the basis Q_0..Q_{i+1}: z = G_0^T ... G_i^T (gv[i+1] e_{i+1})
+    for (int j = 0; j <= i + 1; ++j) c->z[j] = 0.0;
+    c->z[i + 1] = c->gv[i + 1];
+    for (int j = i; j >= 0; --j) {
+      const double zj = c->z[j], zj1 = c->z[j + 1];
+      c->z[j] = c->cs[j] * zj - c->sn[j] * zj1;
+      c->z[j + 1] = c->sn[j] * zj + c->cs[j] * zj1;
+    }
+    for (int j = 0; j <= i + 1; ++j) c->zf[j] = (float)c->z[j];
+  }
+  if (mode == GM_STEP) {
+    c->i = i + 1;
+    c->from_rhs = 0;
+    set_scale(c, 1.0 / hnext);
+  }
+  c->mode = mode;
+}
+
+template <class KT>
+__global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
+  GmresCtl* c = b.ctl;
+  if (*(volatile int*)&c->mode != GM_STEP) return;
+  const int i = c->i, m = i + 1;
+  KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
+  const KT* Q = (const KT*)b.Q;
+  int64_t r0, r1;
+  block_rows(b.S, r0, r1);
+  KT ss = 0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    KT x = w[r];
+    for (int j = 0; j < m; ++j) x = fma(-coef<KT>(c->c2, c->c2f, j), Q[(int64_t)j * b.ldq + r], x);
+    w[r] = x;
+    ss = fma(x, x, ss);
+  }
+  __shared__ KT shr[32];
+  KT bs = block_sum(ss, shr);
+  KT* part = (KT*)b.partials;
+  if (threadIdx.x == 0) part[blockIdx.x] = bs;
+  if (!arrive_last(b.counter)) return;
+  KT t = 0;
+  for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) t += __ldcg(part + bb);
+  t = block_sum(t, shr);
+  if (threadIdx.x == 0) givens_and_decide(c, sqrt((double)t), sizeof(KT) == 4);
+}
+
+// Cheap bound: r = sum_{j<=i} z_j Q_j + z_{i+1} w / hnext equals the residual of the
+// current iterate by the Arnoldi relation J Q_i = Q_{i+1} H (exact arithmetic).
+template <class KT>
+__global__ void __launch_bounds__(RED_THREADS) estimate_kernel(KB b) {
+  GmresCtl* c = b.ctl;
+  if (*(volatile int*)&c->mode != GM_EST) return;
+  const int i = c->i;
+  const KT* w = (const KT*)((i & 1) ? b.w1 : b.w0);
+  const KT* Q = (const KT*)b.Q;
+  const KT zl = coef<KT>(c->z, c->zf, i + 1) * (KT)(1.0 / c->hnext);
+  int64_t r0, r1;
+  block_rows(b.S, r0, r1);
+  KT mx = 0;
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    KT x = zl * w[r];
+    for (int j = 0; j <= i; ++j) x = fma(coef<KT>(c->z, c->zf, j), Q[(int64_t)j * b.ldq + r], x);
+    mx = max(mx, (KT)fabs(x));
+  }
+  __shared__ KT shr[32];
+  KT bm = block_max(mx, shr);
+  KT* part = (KT*)b.partials;
+  if (threadIdx.x == 0) part[blockIdx.x] = bm;
+  if (!arrive_last(b.counter)) return;
+  KT t = 0;
+  for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) t = max(t, __ldcg(part + bb));
+  t = block_max(t, shr);
+  if (threadIdx.x == 0) {
+    c->est_runs += 1;
+    c->last_inf = (double)t;
+    // a small margin keeps rounding in the estimate from skipping a true check
+    if ((double)t <= c->thr * 1.01) c->mode = GM_CHECK;
+    else advance(c);
+  }
+}
+
+// candidate = delta_base + sum_{j<=i} y_j Q_j, into dbuf[1 - dsel].
+template <class KT>
+__global__ void __launch_bounds__(RED_THREADS) candidate_kernel(KB b) {
+  GmresCtl* c = b.ctl;
+  const int mode = *(volatile int*)&c->mode;
+  if (mode != GM_CHECK && mode != GM_RESTART && mode != GM_FINISH) return;
+  const int i = c->i;
+  const KT* base = (const KT*)(c->dsel ? b.d1 : b.d0);
+  KT* cand = (KT*)(c->dsel ? b.d0 : b.d1);
+  const KT* Q = (const KT*)b.Q;
+  int64_t r0, r1;
+  block_rows(b.S, r0, r1);
+  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
+    KT x = base[r];
+    for (int j = 0; j <= i; ++j) x = fma(coef<KT>(c->y, c->yf, j), Q[(int64_t)j * b.ldq + r], x);
+    cand[r] = x;
+  }
+  if (!arrive_last(b.counter)) return;
+  if (threadIdx.x == 0 && mode == GM_FINISH) {
+    c->dsel = 1 - c->dsel;
+    c->mode = GM_DONE;
+  }
+}
+
+__global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double sqrtS, int W,
+                                  int max_steps, const SweepOut* rhs) {
+  c->W = W;
+  c->max_steps = max_steps;
+  c->sqrtS = sqrtS;
+  c->steps = 0;
+  c->restarts = 0;
+  c->est_runs = 0;
+  c->checks = 0;
+  c->i = 0;
+  c->dsel = 0;
+  c->from_rhs = 1;
+  c->status = GS_RUNNING;
+  c->last_inf = rhs->res_inf;
+  c->last_nrm2 = 0.0;
+  c->thr = alpha > 0.0 ? alpha * rhs->res_inf : thr;
+  const double beta = rhs->res_nrm2;
+  c->beta = beta;
+  for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
+  c->gv[0] = beta;
+  set_scale(c, beta > 0.0 ? 1.0 / beta : 0.0);
+  if (!(rhs->res_inf > c->thr) || beta == 0.0) {
+    // the start already meets the stopping rule: the result is delta_base = 0
+    c->mode = GM_DONE;
+    c->status = GS_CONVERGED;
+  } else {
+    c->mode = GM_STEP;
+  }
+}
+
+// v += delta_result (delta_result = dbuf[dsel] once the solve is done)
+template <class KT>
+__global__ void value_update_kernel(double* v, const KT* d0, const KT* d1, const GmresCtl* c,
+                                    const KT* delta, int64_t S) {
+  const KT* dl = delta ? delta : (c->dsel ? d1 : d0);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x)
+    v[s] += (double)dl[s];
+}
+__global__ void value_update_df_kernel(float2* v, const float* d0, const float* d1,
+                                       const GmresCtl* c, const float* delta, int64_t S) {
+  const float* dl = delta ? delta : (c->dsel ? d1 : d0);
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    float2 x = v[s];
+    dfl r = df_add({x.x, x.y}, {dl[s], 0.f});
+    v[s] = make_float2(r.hi, r.lo);
+  }
+}
+
+__global__ void d_to_df_kernel(const double* in, float2* out, int64_t n) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    dfl r = d_to_df(in[s]);
+    out[s] = make_float2(r.hi, r.lo);
+  }
+}
+__global__ void df_to_d_kernel(const float2* in, double* out, int64_t n) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < n;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    float2 x = in[s];
+    out[s] = (double)x.x + (double)x.y;
+  }
+}
+__global__ void cost_transpose_kernel(const double* gAS, double* gSA, float2* gdf, int64_t S,
+                                      int32_t A) {
+  const int64_t n = S * A;
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t s = t / A;
+    const int a = (int)(t - s * A);
+    const double gv = gAS[(int64_t)a * S + s];
+    gSA[t] = gv;
+    if (gdf) {
+      dfl r = d_to_df(gv);
+      gdf[t] = make_float2(r.hi, r.lo);
+    }
+  }
+}
+
+// flags: [0] negative / non-finite probability, [1] column out of range, [2] row sum off,
+//        [3] non-finite cost, [4] state without an allowed action
+template <class PT>
+__global__ void validate_kernel(DevMDP d, int* flags) {
+  const int lane = threadIdx.x & 31;
+  const int64_t nrows = d.S * d.A;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const PT* P = (const PT*)d.P;
+  const double tol = (d.pdt == MDP_F32) ? 1e-5 : 1e-12;
+  const int64_t rowlen = d.kind == KIND_DENSE ? d.ld : d.kp;
+  const int64_t n = d.kind == KIND_DENSE ? d.S : d.k;
+  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
+    const PT* row = P + r * rowlen;
+    double sum = 0.0;
+    int badv = 0, badc = 0;
+    for (int64_t j = lane; j < n; j += 32) {
+      const double x = (double)row[j];
+      if (!(x >= 0.0) || isinf(x)) badv = 1;
+      sum += x;
+      if (d.kind == KIND_ELL) {
+        const int32_t cj = d.col[r * rowlen + j];
+        if (cj < 0 || cj >= d.S) badc = 1;
+      }
+    }
+    sum = warp_sum(sum);
+    badv = __any_sync(0xffffffffu, badv);
+    badc = __any_sync(0xffffffffu, badc);
+    if (lane == 0) {
+      if (badv) atomicOr(flags + 0, 1);
+      if (badc) atomicOr(flags + 1, 1);
+      if (!(fabs(sum - 1.0) <= tol)) atomicOr(flags + 2, 1);
+    }
+  }
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nrows;
+       t += (int64_t)gridDim.x * blockDim.x)
+    if (!isfinite(d.g64[t])) atomicOr(flags + 3, 1);
+  if (d.mask) {
+    for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < d.S;
+         s += (int64_t)gridDim.x * blockDim.x) {
+      int any = 0;
+      for (int a = 0; a < d.A; ++a) any |= d.mask[s * d.A + a] != 0;
+      if (!any) atomicOr(flags + 4, 1);
+    }
+  }
+}
+
+// flags[5] set when some pi(s) is outside [0, A) or not an allowed action
+__global__ void check_policy_kernel(const int32_t* pi, int64_t S, int32_t A, const uint8_t* mask,
+                                    int* flags) {
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = pi[s];
+    if (a < 0 || a >= A || (mask && mask[s * A + a] == 0)) atomicOr(flags + 5, 1);
+  }
+}
+
+inline int ew_grid(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, (int64_t)num_sms() * 8));
+}
+
+inline int ok_or_dev() { return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE; }
+
+KB make_kb(const KrylovBufs& B) {
+  return KB{B.S, B.ldq, B.Q, B.w0, B.w1, B.rbuf, B.d0, B.d1, B.partials, B.counter, B.ctl};
+}
+
+}  // namespace
+
+int launch_matvec(const MatvecLaunch& L, cudaStream_t st) {
+  if (L.kt == 1) {
+    if (L.d.pdt != MDP_F32) return MDP_EINVAL;
+    return launch_mv_typed<float, float>(L, st);
+  }
+  if (L.d.pdt == MDP_F32) return launch_mv_typed<float, double>(L, st);
+  return launch_mv_typed<double, double>(L, st);
+}
+
+int launch_cgs2_givens(const KrylovBufs& B, cudaStream_t st) {
+  KB b = make_kb(B);
+  if (B.kt == 1) {
+    cgs_dots_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
+    cgs_axpy_dots_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
+    cgs_axpy_norm_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
+  } else {
+    cgs_dots_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+    cgs_axpy_dots_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+    cgs_axpy_norm_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+  }
+  return ok_or_dev();
+}
+
+int launch_estimate(const KrylovBufs& B, cudaStream_t st) {
+  KB b = make_kb(B);
+  if (B.kt == 1) estimate_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
+  else estimate_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+  return ok_or_dev();
+}
+
+int launch_candidate(const KrylovBufs& B, cudaStream_t st) {
+  KB b = make_kb(B);
+  if (B.kt == 1) candidate_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
+  else candidate_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+  return ok_or_dev();
+}
+
+int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
+                      const SweepOut* rhs_norms, double alpha, cudaStream_t st) {
+  gmres_init_kernel<<<1, 1, 0, st>>>(B.ctl, thr, alpha, sqrtS, W, max_steps, rhs_norms);
+  return ok_or_dev();
+}
+
+int launch_value_update(int kt, void* v, const void* d0, const void* d1, const GmresCtl* ctl,
+                        const void* delta, int64_t S, cudaStream_t st) {
+  if (kt == 1)
+    value_update_df_kernel<<<ew_grid(S), 256, 0, st>>>((float2*)v, (const float*)d0,
+                                                        (const float*)d1, ctl,
+                                                        (const float*)delta, S);
+  else
+    value_update_kernel<double><<<ew_grid(S), 256, 0, st>>>((double*)v, (const double*)d0,
+                                                            (const double*)d1, ctl,
+                                                            (const double*)delta, S);
+  return ok_or_dev();
+}
+
+int launch_d_to_df(const double* in, float2* out, int64_t n, cudaStream_t st) {
+  d_to_df_kernel<<<ew_grid(n), 256, 0, st>>>(in, out, n);
+  return ok_or_dev();
+}
+int launch_df_to_d(const float2* in, double* out, int64_t n, cudaStream_t st) {
+  df_to_d_kernel<<<ew_grid(n), 256, 0, st>>>(in, out, n);
+  return ok_or_dev();
+}
+int launch_fill_zero(void* p, size_t bytes, cudaStream_t st) {
+  return cudaMemsetAsync(p, 0, bytes, st) == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+int launch_cost_transpose(const double* gAS, double* gSA, float2* gdf, int64_t S, int32_t A,
+                          cudaStream_t st) {
+  cost_transpose_kernel<<<ew_grid(S * A), 256, 0, st>>>(gAS, gSA, gdf, S, A);
+  return ok_or_dev();
+}
+int launch_validate(const DevMDP& d, int* flags, cudaStream_t st) {
+  const int64_t rows = d.S * d.A;
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((rows + 7) / 8, (int64_t)num_sms() * 16));
+  if (d.pdt == MDP_F32) validate_kernel<float><<<grid, 256, 0, st>>>(d, flags);
+  else validate_kernel<double><<<grid, 256, 0, st>>>(d, flags);
+  return ok_or_dev();
+}
+
+int launch_check_policy(const int32_t* pi, int64_t S, int32_t A, const uint8_t* mask, int* flags,
+                        cudaStream_t st) {
+  check_policy_kernel<<<ew_grid(S), 256, 0, st>>>(pi, S, A, mask, flags);
+  return ok_or_dev();
+}
+
+int num_sms() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+  }
+  return n;
+}
+
+}  // namespace mdp

@@ -1,0 +1,330 @@
+// Internal declarations shared by the CUDA translation units of libmdpgpu.
+//
+// Device data layout (chosen at upload, independent of the caller's layout):
+//   dense P : [S][A][ld]   state-major, ld = S rounded up to 4 (FP32) / 2 (FP64) elements,
+//                          pad columns zero; a state's A rows are one contiguous stream.
+//   ELL     : val, col [S][A][kp], kp = k rounded up to 4; pad entries val 0, col 0.
+//   g       : [S][A] FP64, plus a double-float copy [S][A] for the mixed path.
+//   mask    : [S][A] bytes or null.
+// Value vectors of the FP64 path are double[ldv]; of the mixed path float2 (hi, lo)
+// double-float pairs.  Krylov vectors are double (FP64 path) or float (mixed path),
+// [W+1][ldq] with ldq a multiple of 32 elements.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mdpgpu.h"
+
+namespace mdp {
+
+constexpr int WMAX = 64;          // largest GMRES restart length
+constexpr int RED_THREADS = 256;  // threads of every reduction-carrying kernel
+constexpr int MAX_RED_BLOCKS = 2048;
+
+enum Kind { KIND_DENSE = 0, KIND_ELL = 1 };
+
+// Read-only view of a handle's transition data on the device.
+struct DevMDP {
+  int64_t S;
+  int32_t A;
+  int32_t k;
+  int32_t kp;      // padded ELL row length
+  int64_t ld;      // padded dense row length
+  int32_t kind;
+  int32_t pdt;     // MDP_F32 / MDP_F64
+  double gamma;
+  float gamma_hi, gamma_lo;
+  const void* P;       // dense P or ELL val
+  const int32_t* col;  // ELL columns
+  const double* g64;   // [S][A]
+  const float2* gdf;   // [S][A] double-float copy (FP32 P only)
+  const uint8_t* mask; // [S][A] or null
+};
+
+// ------------------------------------------------------------------ double-float arithmetic
+// Error-free transforms (Knuth's TwoSum, Dekker's Fast2Sum, FMA-based TwoProduct) and the
+// double-word sum/product of Joldes, Muller & Popescu (ACM TOMS 2017).  The *_rn
+// intrinsics keep the compiler from contracting the steps into FMAs.
+struct dfl { float hi, lo; };
+
+__device__ __forceinline__ dfl two_sum(float a, float b) {
+  float s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return {s, e};
+}
+__device__ __forceinline__ dfl fast_two_sum(float a, float b) {  // needs |a| >= |b| or a == 0
+  float s = __fadd_rn(a, b);
+  float e = __fsub_rn(b, __fsub_rn(s, a));
+  return {s, e};
+}
+__device__ __forceinline__ dfl two_prod(float a, float b) {
+  float p = __fmul_rn(a, b);
+  return {p, __fmaf_rn(a, b, -p)};
+}
+__device__ __forceinline__ dfl df_add(dfl x, dfl y) {
+  dfl s = two_sum(x.hi, y.hi);
+  dfl t = two_sum(x.lo, y.lo);
+  dfl v = fast_two_sum(s.hi, __fadd_rn(s.lo, t.hi));
+  return fast_two_sum(v.hi, __fadd_rn(t.lo, v.lo));
+}
+__device__ __forceinline__ dfl df_neg(dfl x) { return {-x.hi, -x.lo}; }
+__device__ __forceinline__ dfl df_sub(dfl x, dfl y) { return df_add(x, df_neg(y)); }
+__device__ __forceinline__ dfl df_mul(dfl x, dfl y) {
+  dfl c = two_prod(x.hi, y.hi);
+  float t = __fmaf_rn(x.lo, y.hi, __fmul_rn(x.hi, y.lo));
+  return fast_two_sum(c.hi, __fadd_rn(c.lo, t));
+}
+__device__ __forceinline__ dfl df_mul_f(dfl x, float b) {  // double-float times float
+  dfl c = two_prod(x.hi, b);
+  return fast_two_sum(c.hi, __fmaf_rn(x.lo, b, c.lo));
+}
+__device__ __forceinline__ bool df_lt(dfl a, dfl b) {
+  return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo);
+}
+__device__ __forceinline__ double df_to_d(dfl x) { return (double)x.hi + (double)x.lo; }
+__device__ __forceinline__ dfl d_to_df(double d) {
+  float hi = (float)d;
+  return {hi, (float)(d - (double)hi)};
+}
+__device__ __forceinline__ dfl shfl_xor_df(dfl x, int off) {
+  return {__shfl_xor_sync(0xffffffffu, x.hi, off), __shfl_xor_sync(0xffffffffu, x.lo, off)};
+}
+
+// Running sum of products p * v with p FP32 and v double-float, accurate to about 2^-48
+// relative: each product is split exactly (TwoProduct), the high parts are added with
+// TwoSum and every error term goes to a low word; every 32 terms the chunk is folded into
+// a double-word total so the low word never grows long.
+struct AccDF {
+  float sh, sl;
+  dfl tot;
+  int n;
+  __device__ __forceinline__ void init() { sh = 0.f; sl = 0.f; tot = {0.f, 0.f}; n = 0; }
+  __device__ __forceinline__ void add(float p, float2 v) {
+    float ph = __fmul_rn(p, v.x);
+    float pe = __fmaf_rn(p, v.x, -ph);
+    dfl s = two_sum(sh, ph);
+    sh = s.hi;
+    sl = __fadd_rn(sl, __fadd_rn(s.lo, __fmaf_rn(p, v.y, pe)));
+  }
+  __device__ __forceinline__ void tick() {
+    if (++n == 8) fold();
+  }
+  __device__ __forceinline__ void fold() {
+    tot = df_add(tot, two_sum(sh, sl));
+    sh = 0.f; sl = 0.f; n = 0;
+  }
+  __device__ __forceinline__ dfl result() {
+    fold();
+    return tot;
+  }
+};
+
+// ------------------------------------------------------------------ small helpers
+template <typename T> __device__ __forceinline__ T warp_sum(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+  return x;
+}
+template <typename T> __device__ __forceinline__ T warp_max(T x) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = max(x, __shfl_xor_sync(0xffffffffu, x, o));
+  return x;
+}
+
+// Block-wide sum/max of one value per thread (blockDim.x == RED_THREADS); result valid in
+// every thread.  Uses sh[32].
+template <typename T> __device__ __forceinline__ T block_sum(T x, T* sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  x = warp_sum(x);
+  __syncthreads();
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  T r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) r = warp_sum(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+template <typename T> __device__ __forceinline__ T block_max(T x, T* sh) {
+  int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  x = warp_max(x);
+  __syncthreads();
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  T r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : T(0);
+  if (wid == 0) r = warp_max(r);
+  if (threadIdx.x == 0) sh[0] = r;
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// "Last block done" detection for single-pass grid reductions: every block stores its
+// partial results, then calls this; it returns true in exactly one block (the last to
+// arrive), which may then read all partials.  That block resets the counter to zero, so a
+// counter that starts at zero is zero again after every launch.
+__device__ __forceinline__ bool arrive_last(unsigned* counter) {
+  __shared__ bool am_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(counter, 1u);
+    am_last = (t == gridDim.x - 1);
+    if (am_last) *counter = 0u;
+  }
+  __syncthreads();
+  if (am_last) __threadfence();
+  return am_last;
+}
+
+// ------------------------------------------------------------------ GMRES control block
+// Modes of the device-resident inner-solver state machine.  Each kernel of an Arnoldi step
+// runs only in the modes listed beside it and returns at once otherwise, so a whole step
+// can be enqueued (or replayed from a graph) without the host looking at the state.
+enum GmresMode {
+  GM_STEP = 0,      // matvec + CGS2 + Givens of step i are due
+  GM_EST = 1,       // Givens estimate passed the gate: estimate ||r||_inf from Q z
+  GM_CHECK = 2,     // estimate passed: form the candidate and test the true residual
+  GM_RESTART = 3,   // cycle full: form the candidate, restart from its true residual
+  GM_FINISH = 4,    // breakdown or step cap: form the candidate and stop
+  GM_DONE = 5,      // candidate accepted (ctl.status says why)
+  GM_IDLE = 6
+};
+
+enum GmresStatus { GS_RUNNING = 0, GS_CONVERGED = 1, GS_BREAKDOWN = 2, GS_CAP = 3 };
+
+struct GmresCtl {
+  int mode;
+  int status;
+  int i;            // current Arnoldi index: Q_0..Q_i exist, Q_i is normalised
+  int W;            // restart length
+  int steps;        // Arnoldi steps so far (all cycles)
+  int max_steps;
+  int restarts;
+  int dsel;         // delta_base = dbuf[dsel], candidate = dbuf[1 - dsel]
+  int from_rhs;     // step 0 of a cycle reads its start vector from rbuf (scaled by 1/beta)
+  int est_runs, checks, pad_;
+  double thr;       // target on the inf-norm of the residual
+  double sqrtS;
+  double beta;      // 2-norm of the cycle's start residual
+  double rho;       // |gv[i+1]| = least-squares residual estimate
+  double hnext;     // H[i+1][i]
+  double xscale;    // scale of the vector the next matvec reads (1/beta or 1/hnext)
+  double last_inf;  // last inf-norm computed (estimate or true residual)
+  double last_nrm2;
+  double H[(WMAX + 1) * WMAX];  // column-major, leading dimension WMAX+1
+  double cs[WMAX], sn[WMAX];
+  double gv[WMAX + 1];
+  double y[WMAX];
+  double z[WMAX + 1];
+  double c1[WMAX + 1], c2[WMAX + 1];  // CGS2 coefficients of pass 1 and pass 2
+  float c1f[WMAX + 1], c2f[WMAX + 1], yf[WMAX], zf[WMAX + 1];
+  float xscalef;
+};
+
+// Scalars produced by the Bellman sweep and by reduction kernels.
+struct SweepOut {
+  double res_inf;   // ||Phi||_inf
+  double res_nrm2;  // ||Phi||_2
+};
+
+// ------------------------------------------------------------------ launch descriptors
+struct SweepLaunch {
+  DevMDP d;
+  int arith;            // 0: FP64, 1: double-float (needs FP32 P)
+  const void* v;        // value vector (double or float2)
+  const int32_t* pi_in; // optional: evaluate only row pi_in(s) (T^pi v)
+  int32_t* pi_out;
+  void* tv_out;         // same type as v
+  double* tv64_out;
+  void* phi_out;        // Krylov type: double (arith 0) or float (arith 1)
+  double* margin_out;
+  const int32_t* pi_ref;// optional: residual of this policy at v
+  void* rref_out;       // Krylov type: g^pi_ref + gamma P^pi_ref v - v
+  SweepOut* out;
+  void* partials;       // >= MAX_RED_BLOCKS * 4 doubles
+  unsigned* counter;
+  int lanes;            // ELL lanes per row (1,2,4,8); 0 = choose
+  int grid;             // 0 = choose
+};
+
+int launch_sweep(const SweepLaunch& L, cudaStream_t st);
+
+struct MatvecLaunch {
+  DevMDP d;
+  int kt;               // Krylov type: 0 double, 1 float
+  const int32_t* pi;
+  const void* x;        // input vector (kt), scaled by *xscale_d / *xscale_f if given
+  const GmresCtl* ctl;  // when set: gate on ctl->mode and take x / scale from the control
+  int gate_mode;        // run only if ctl->mode == gate_mode (or gate_mode2)
+  int gate_mode2;
+  const void* x_rhs;    // cycle start vector (ctl->from_rhs)
+  const void* x_w0;     // previous step's w, buffer for even steps
+  const void* x_w1;     // ... odd steps
+  void* qbase;          // Krylov basis [W+1][ldq]: the normalised input is written to Q_i
+  int64_t ldq;
+  double a, b, c;       // out = a*x + b*u + c*(P^pi x)
+  const void* u;
+  void* out;            // or chosen by parity when ctl is set
+  void* out0;
+  void* out1;
+  SweepOut* norms;      // optional inf/2-norm of out
+  GmresCtl* ctl_rw;     // when set (with gate CHECK/RESTART): finalise the check
+  void* partials;
+  unsigned* counter;
+  int lanes;
+  int grid;
+};
+
+int launch_matvec(const MatvecLaunch& L, cudaStream_t st);
+
+struct KrylovBufs {
+  int kt;         // 0 double, 1 float
+  int64_t S;
+  int64_t ldq;
+  void* Q;        // [W+1][ldq]
+  void* w0;       // w buffers (parity of i)
+  void* w1;
+  void* rbuf;     // cycle start residual
+  void* d0;       // delta buffers
+  void* d1;
+  void* partials;
+  unsigned* counter;
+  GmresCtl* ctl;
+  int grid;
+};
+
+// One Arnoldi step after the matvec: CGS2 (two passes) + norm + Givens + mode decision.
+int launch_cgs2_givens(const KrylovBufs& B, cudaStream_t st);
+// Gated on GM_EST: ||Q_{0..i} z + z_{i+1} w / hnext||_inf, then decide CHECK or not.
+int launch_estimate(const KrylovBufs& B, cudaStream_t st);
+// Gated on CHECK/RESTART/FINISH: candidate = delta_base + Q_{0..i} y.
+int launch_candidate(const KrylovBufs& B, cudaStream_t st);
+// Initialise the control block for a new inner solve (device side, no host copy).
+int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
+                      const SweepOut* rhs_norms, double alpha, cudaStream_t st);
+
+// Value update v += delta (double or double-float), delta = chosen by ctl (or given).
+int launch_value_update(int kt, void* v, const void* d0, const void* d1, const GmresCtl* ctl,
+                        const void* delta, int64_t S, cudaStream_t st);
+// Conversions between double and double-float vectors, and fills.
+int launch_d_to_df(const double* in, float2* out, int64_t n, cudaStream_t st);
+int launch_df_to_d(const float2* in, double* out, int64_t n, cudaStream_t st);
+int launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
+// Transpose [A][S] -> [S][A] for g (and produce the double-float copy when gdf != null).
+int launch_cost_transpose(const double* gAS, double* gSA, float2* gdf, int64_t S, int32_t A,
+                          cudaStream_t st);
+// Device-side validation of uploaded data; writes error flags into *flags (4 ints).
+int launch_validate(const DevMDP& d, int* flags, cudaStream_t st);
+// flags[5] |= 1 when a policy entry is out of range or disallowed by the mask.
+int launch_check_policy(const int32_t* pi, int64_t S, int32_t A, const uint8_t* mask, int* flags,
+                        cudaStream_t st);
+
+int num_sms();
+
+}  // namespace mdp

@@ -1,0 +1,438 @@
+// Fused Bellman sweep (paper Sec. 2, Bellman operators T^pi and T; Alg. 2 steps
+// "pi_k <- GreedyPolicy(V_k)" and "Phi_k <- g^pi_k - J^pi_k V_k"):
+//
+//   Q(s,a) = g(s,a) + gamma * sum_s' p_ss'(a) v(s')
+//   pi(s)  = lowest a in A(s) with minimal Q(s,a),  Tv(s) = Q(s, pi(s)),
+//   Phi(s) = Tv(s) - v(s),   ||Phi||_inf, ||Phi||_2,   margin(s) = Q2(s) - Q1(s)
+//
+// One pass over every P_a row.  With pi_in set the sweep evaluates only row pi_in(s)
+// (T^pi v).  Two arithmetics: FP64 (P in FP32 or FP64, v double) and double-float (P FP32,
+// v as float2 hi/lo pairs, all sums on the FP32 pipes, ~2^-48 relative).
+#include "mdp_internal.cuh"
+
+#include <algorithm>
+
+namespace mdp {
+
+namespace {
+
+// ------------------------------------------------------------------ arithmetic traits
+struct ArF64 {
+  using V = double;   // value vector element
+  using Qt = double;  // Q value
+  using K = double;   // Krylov element
+  using R = double;   // reduction type
+  struct Acc {
+    double s;
+    __device__ __forceinline__ void init() { s = 0.0; }
+    __device__ __forceinline__ void add(double p, double v) { s = fma(p, v, s); }
+    __device__ __forceinline__ void add(float p, double v) { s = fma((double)p, v, s); }
+    __device__ __forceinline__ void fold() {}
+    __device__ __forceinline__ double result() { return s; }
+  };
+  static __device__ __forceinline__ Qt reduce_team(Qt x, int T) {
+    for (int o = T >> 1; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    return x;
+  }
+  static __device__ __forceinline__ Qt qval(const DevMDP& d, int64_t s, int a, Qt sum) {
+    return fma(d.gamma, sum, d.g64[s * d.A + a]);
+  }
+  static __device__ __forceinline__ Qt inf() { return __longlong_as_double(0x7ff0000000000000LL); }
+  static __device__ __forceinline__ bool lt(Qt a, Qt b) { return a < b; }
+  static __device__ __forceinline__ Qt sub(Qt a, V b) { return a - b; }
+  static __device__ __forceinline__ Qt subq(Qt a, Qt b) { return a - b; }
+  static __device__ __forceinline__ double to_d(Qt a) { return a; }
+  static __device__ __forceinline__ K to_k(Qt a) { return a; }
+  static __device__ __forceinline__ V to_v(Qt a) { return a; }
+  static __device__ __forceinline__ R absr(Qt a) { return fabs(a); }
+  static __device__ __forceinline__ V load_v(const V* v, int64_t i) { return __ldg(v + i); }
+  // running maximum of |Phi| (exact comparison in the arithmetic's own precision)
+  using MaxT = double;
+  static __device__ __forceinline__ MaxT max0() { return 0.0; }
+  static __device__ __forceinline__ MaxT absq(Qt a) { return fabs(a); }
+  static __device__ __forceinline__ MaxT mmax(MaxT a, MaxT b) { return max(a, b); }
+  static __device__ __forceinline__ MaxT shfl(MaxT a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+  static __device__ __forceinline__ double mtod(MaxT a) { return a; }
+};
+
+struct ArDF {
+  using V = float2;
+  using Qt = dfl;
+  using K = float;
+  using R = float;
+  struct Acc {
+    AccDF a;
+    __device__ __forceinline__ void init() { a.init(); }
+    __device__ __forceinline__ void add(float p, float2 v) { a.add(p, v); }
+    __device__ __forceinline__ void fold() { a.fold(); }
+    __device__ __forceinline__ dfl result() { return a.result(); }
+  };
+  static __device__ __forceinline__ Qt reduce_team(Qt x, int T) {
+    for (int o = T >> 1; o > 0; o >>= 1) x = df_add(x, shfl_xor_df(x, o));
+    return x;
+  }
+  static __device__ __forceinline__ Qt qval(const DevMDP& d, int64_t s, int a, Qt sum) {
+    float2 g = __ldg(d.gdf + s * d.A + a);
+    return df_add({g.x, g.y}, df_mul(dfl{d.gamma_hi, d.gamma_lo}, sum));
+  }
+  static __device__ __forceinline__ Qt inf() { return {__int_as_float(0x7f800000), 0.f}; }
+  static __device__ __forceinline__ bool lt(Qt a, Qt b) { return df_lt(a, b); }
+  static __device__ __forceinline__ Qt sub(Qt a, V b) { return df_sub(a, dfl{b.x, b.y}); }
+  static __device__ __forceinline__ Qt subq(Qt a, Qt b) { return df_sub(a, b); }
+  static __device__ __forceinline__ double to_d(Qt a) { return df_to_d(a); }
+  static __device__ __forceinline__ K to_k(Qt a) { return __fadd_rn(a.hi, a.lo); }
+  static __device__ __forceinline__ V to_v(Qt a) { return make_float2(a.hi, a.lo); }
+  static __device__ __forceinline__ R absr(Qt a) { return fabsf(__fadd_rn(a.hi, a.lo)); }
+  static __device__ __forceinline__ V load_v(const V* v, int64_t i) { return __ldg(v + i); }
+  using MaxT = dfl;
+  static __device__ __forceinline__ MaxT max0() { return {0.f, 0.f}; }
+  static __device__ __forceinline__ MaxT absq(Qt a) { return a.hi < 0.f ? df_neg(a) : a; }
+  static __device__ __forceinline__ MaxT mmax(MaxT a, MaxT b) { return df_lt(a, b) ? b : a; }
+  static __device__ __forceinline__ MaxT shfl(MaxT a, int o) { return shfl_xor_df(a, o); }
+  static __device__ __forceinline__ double mtod(MaxT a) { return df_to_d(a); }
+};
+
+struct SweepK {
+  DevMDP d;
+  const void* v;
+  const int32_t* pi_in;
+  int32_t* pi_out;
+  void* tv_out;
+  double* tv64_out;
+  void* phi_out;
+  double* margin_out;
+  const int32_t* pi_ref;
+  void* rref_out;
+  SweepOut* out;
+  void* partials;
+  unsigned* counter;
+};
+
+// Running argmin over the actions of one state, lowest index on exact ties.
+template <class AR> struct Pick {
+  typename AR::Qt best, second, qref;
+  int abest;
+  __device__ __forceinline__ void init() {
+    best = AR::inf(); second = AR::inf(); qref = AR::inf(); abest = -1;
+  }
+  __device__ __forceinline__ void consider(int a, typename AR::Qt q, bool allowed, int aref) {
+    if (a == aref) qref = q;
+    if (!allowed) return;
+    if (AR::lt(q, best) || abest < 0) {
+      second = best; best = q; abest = a;
+    } else if (AR::lt(q, second)) {
+      second = q;
+    }
+  }
+};
+
+template <class AR>
+__device__ __forceinline__ void emit_state(const SweepK& p, int64_t s, const Pick<AR>& pk,
+                                           typename AR::MaxT& mx, typename AR::R& ss) {
+  using V = typename AR::V;
+  using K = typename AR::K;
+  const V vs = AR::load_v((const V*)p.v, s);
+  const typename AR::Qt phi = AR::sub(pk.best, vs);
+  int a = pk.abest < 0 ? 0 : pk.abest;
+  if (p.pi_in) a = p.pi_in[s];
+  if (p.pi_out) p.pi_out[s] = a;
+  if (p.tv_out) ((V*)p.tv_out)[s] = AR::to_v(pk.best);
+  if (p.tv64_out) p.tv64_out[s] = AR::to_d(pk.best);
+  if (p.phi_out) ((K*)p.phi_out)[s] = AR::to_k(phi);
+  if (p.margin_out) {
+    double m = AR::to_d(pk.second);
+    p.margin_out[s] = isinf(m) ? m : AR::to_d(AR::subq(pk.second, pk.best));
+  }
+  if (p.rref_out) ((K*)p.rref_out)[s] = AR::to_k(AR::sub(pk.qref, vs));
+  typename AR::R r = AR::absr(phi);
+  mx = AR::mmax(mx, AR::absq(phi));
+  ss += r * r;
+}
+
+template <class AR>
+__device__ __forceinline__ typename AR::MaxT block_maxq(typename AR::MaxT x, typename AR::MaxT* sh) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) x = AR::mmax(x, AR::shfl(x, o));
+  __syncthreads();
+  if (lane == 0) sh[wid] = x;
+  __syncthreads();
+  typename AR::MaxT r = (threadIdx.x < (blockDim.x >> 5)) ? sh[threadIdx.x] : AR::max0();
+  if (wid == 0) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) r = AR::mmax(r, AR::shfl(r, o));
+    if (lane == 0) sh[0] = r;
+  }
+  __syncthreads();
+  r = sh[0];
+  __syncthreads();
+  return r;
+}
+
+// Block partial -> last block -> out->res_inf / res_nrm2.  Partials hold the block maximum
+// (MaxT) and the block sum of squares (R) in slots of 8 bytes each.
+template <class AR>
+__device__ __forceinline__ void finish_norms(const SweepK& p, typename AR::MaxT mx,
+                                             typename AR::R ss) {
+  using R = typename AR::R;
+  using M = typename AR::MaxT;
+  __shared__ M shm[32];
+  __shared__ R shr[32];
+  M bm = block_maxq<AR>(mx, shm);
+  R bs = block_sum(ss, shr);
+  M* pm = (M*)p.partials;
+  R* ps = (R*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 8);
+  if (threadIdx.x == 0) {
+    pm[blockIdx.x] = bm;
+    ps[blockIdx.x] = bs;
+  }
+  if (!arrive_last(p.counter)) return;
+  M m = AR::max0();
+  R t = 0;
+  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+    M x;
+    if constexpr (sizeof(M) == 8 && sizeof(R) == 8) x = __ldcg((const double*)pm + b);
+    else { float2 f = __ldcg((const float2*)pm + b); x = M{f.x, f.y}; }
+    m = AR::mmax(m, x);
+    t += __ldcg(ps + b);
+  }
+  m = block_maxq<AR>(m, shm);
+  t = block_sum(t, shr);
+  if (threadIdx.x == 0 && p.out) {
+    p.out->res_inf = AR::mtod(m);
+    p.out->res_nrm2 = sqrt((double)t);
+  }
+}
+
+// ------------------------------------------------------------------ dense: warp per state
+template <class PT> struct Vec4;
+template <> struct Vec4<float> {
+  float e[4];
+  __device__ __forceinline__ void load(const float* p) {
+    float4 t = __ldcs(reinterpret_cast<const float4*>(p));
+    e[0] = t.x; e[1] = t.y; e[2] = t.z; e[3] = t.w;
+  }
+};
+template <> struct Vec4<double> {
+  double e[4];
+  __device__ __forceinline__ void load(const double* p) {
+    double2 t0 = __ldcs(reinterpret_cast<const double2*>(p));
+    double2 t1 = __ldcs(reinterpret_cast<const double2*>(p) + 1);
+    e[0] = t0.x; e[1] = t0.y; e[2] = t1.x; e[3] = t1.y;
+  }
+};
+
+template <class V> struct VLoad4;
+template <> struct VLoad4<double> {
+  double e[4];
+  __device__ __forceinline__ void load(const double* v) {
+    double2 t0 = __ldg(reinterpret_cast<const double2*>(v));
+    double2 t1 = __ldg(reinterpret_cast<const double2*>(v) + 1);
+    e[0] = t0.x; e[1] = t0.y; e[2] = t1.x; e[3] = t1.y;
+  }
+};
+template <> struct VLoad4<float2> {
+  float2 e[4];
+  __device__ __forceinline__ void load(const float2* v) {
+    float4 t0 = __ldg(reinterpret_cast<const float4*>(v));
+    float4 t1 = __ldg(reinterpret_cast<const float4*>(v) + 1);
+    e[0] = make_float2(t0.x, t0.y); e[1] = make_float2(t0.z, t0.w);
+    e[2] = make_float2(t1.x, t1.y); e[3] = make_float2(t1.z, t1.w);
+  }
+};
+
+template <class PT, class AR, int AG>
+__global__ void __launch_bounds__(256) sweep_dense_kernel(SweepK p) {
+  using V = typename AR::V;
+  using Qt = typename AR::Qt;
+  const DevMDP& d = p.d;
+  const int lane = threadIdx.x & 31;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int R = p.pi_in ? 1 : d.A;
+  const PT* P = (const PT*)d.P;
+  const V* v = (const V*)p.v;
+  typename AR::MaxT mx = AR::max0();
+  typename AR::R ss = 0;
+  for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < d.S; s += nw) {
+    Pick<AR> pk;
+    pk.init();
+    const int aref = p.pi_ref ? p.pi_ref[s] : -1;
+    for (int a0 = 0; a0 < R; a0 += AG) {
+      const int na = min(AG, R - a0);
+      const PT* row[AG];
+#pragma unroll
+      for (int g = 0; g < AG; ++g) {
+        int a = p.pi_in ? p.pi_in[s] : min(a0 + g, d.A - 1);
+        row[g] = P + ((int64_t)s * d.A + a) * d.ld;
+      }
+      typename AR::Acc acc[AG];
+#pragma unroll
+      for (int g = 0; g < AG; ++g) acc[g].init();
+      int it = 0;
+      for (int64_t c = 4 * lane; c < d.ld; c += 128) {
+        VLoad4<V> vv;
+        vv.load(v + c);
+        Vec4<PT> pv[AG];
+#pragma unroll
+        for (int g = 0; g < AG; ++g)
+          if (g < na) pv[g].load(row[g] + c);
+#pragma unroll
+        for (int g = 0; g < AG; ++g) {
+          if (g < na) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc[g].add(pv[g].e[e], vv.e[e]);
+          }
+        }
+        if ((++it & 7) == 0) {
+#pragma unroll
+          for (int g = 0; g < AG; ++g) acc[g].fold();
+        }
+      }
+#pragma unroll
+      for (int g = 0; g < AG; ++g) {
+        Qt sum = AR::reduce_team(acc[g].result(), 32);
+        if (g < na) {
+          int a = p.pi_in ? p.pi_in[s] : a0 + g;
+          bool allowed = p.pi_in ? true : (d.mask ? d.mask[s * d.A + a] != 0 : true);
+          pk.consider(a, AR::qval(d, s, a, sum), allowed, aref);
+        }
+      }
+    }
+    if (lane == 0) emit_state<AR>(p, s, pk, mx, ss);
+  }
+  finish_norms<AR>(p, mx, ss);
+}
+
+// ------------------------------------------------------------------ ELL: lane teams per row
+template <class PT, class AR, int T>
+__global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
+  using V = typename AR::V;
+  using Qt = typename AR::Qt;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  Qt* Qsm = reinterpret_cast<Qt*>(smem_raw);
+  const DevMDP& d = p.d;
+  const int nteams = blockDim.x / T;
+  const int team = threadIdx.x / T, tl = threadIdx.x % T;
+  const int R = p.pi_in ? 1 : d.A;
+  const int SB = max(1, nteams / R);
+  const int64_t ntiles = (d.S + SB - 1) / SB;
+  const PT* val = (const PT*)d.P;
+  const int32_t* col = d.col;
+  const V* v = (const V*)p.v;
+  const int nvec = d.kp >> 2;
+  typename AR::MaxT mx = AR::max0();
+  typename AR::R ss = 0;
+  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    const int64_t s0 = tile * SB;
+    const int ns = (int)((d.S - s0) < (int64_t)SB ? (d.S - s0) : (int64_t)SB);
+    const int nrows = ns * R;
+    for (int rb = 0; rb < nrows; rb += nteams) {
+      const int r = rb + team;
+      const bool act = r < nrows;
+      typename AR::Acc acc;
+      acc.init();
+      if (act) {
+        const int64_t s = s0 + r / R;
+        const int a = p.pi_in ? p.pi_in[s] : r % R;
+        const int64_t base = ((int64_t)s * d.A + a) * d.kp;
+        int it = 0;
+        for (int q = tl; q < nvec; q += T) {
+          Vec4<PT> pv;
+          pv.load(val + base + 4 * q);
+          int4 c4 = __ldcs(reinterpret_cast<const int4*>(col + base) + q);
+          acc.add(pv.e[0], AR::load_v(v, c4.x));
+          acc.add(pv.e[1], AR::load_v(v, c4.y));
+          acc.add(pv.e[2], AR::load_v(v, c4.z));
+          acc.add(pv.e[3], AR::load_v(v, c4.w));
+          if ((++it & 7) == 0) acc.fold();
+        }
+      }
+      Qt sum = AR::reduce_team(acc.result(), T);
+      if (act && tl == 0) {
+        const int64_t s = s0 + r / R;
+        const int a = p.pi_in ? p.pi_in[s] : r % R;
+        Qsm[r] = AR::qval(d, s, a, sum);
+      }
+    }
+    __syncthreads();
+    for (int st = threadIdx.x; st < ns; st += blockDim.x) {
+      const int64_t s = s0 + st;
+      Pick<AR> pk;
+      pk.init();
+      const int aref = p.pi_ref ? p.pi_ref[s] : -1;
+      if (p.pi_in) {
+        pk.consider(p.pi_in[s], Qsm[st], true, -1);
+      } else {
+        for (int a = 0; a < R; ++a)
+          pk.consider(a, Qsm[st * R + a], d.mask ? d.mask[s * d.A + a] != 0 : true, aref);
+      }
+      emit_state<AR>(p, s, pk, mx, ss);
+    }
+    __syncthreads();
+  }
+  finish_norms<AR>(p, mx, ss);
+}
+
+template <class Kern>
+int grid_for(Kern k, int threads, size_t smem, int64_t work_units) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, threads, smem) != cudaSuccess)
+    per_sm = 1;
+  per_sm = std::max(per_sm, 1);
+  int64_t g = (int64_t)num_sms() * per_sm;
+  g = std::min<int64_t>(g, std::max<int64_t>(work_units, 1));
+  g = std::min<int64_t>(g, MAX_RED_BLOCKS);
+  return (int)std::max<int64_t>(g, 1);
+}
+
+template <class PT, class AR>
+int launch_typed(const SweepLaunch& L, cudaStream_t st) {
+  SweepK p{L.d, L.v, L.pi_in, L.pi_out, L.tv_out, L.tv64_out, L.phi_out, L.margin_out,
+           L.pi_ref, L.rref_out, L.out, L.partials, L.counter};
+  const DevMDP& d = L.d;
+  if (d.kind == KIND_DENSE) {
+    auto k = sweep_dense_kernel<PT, AR, 8>;
+    int grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, (d.S + 7) / 8);
+    k<<<grid, 256, 0, st>>>(p);
+  } else {
+    int T = L.lanes;
+    if (T <= 0) {
+      int nvec = d.kp / 4;
+      T = nvec >= 8 ? 2 : 1;
+    }
+    const int R = L.pi_in ? 1 : d.A;
+    const int SB = std::max(1, (256 / T) / R);
+    const size_t smem = (size_t)SB * R * sizeof(typename AR::Qt);
+    const int64_t ntiles = (d.S + SB - 1) / SB;
+    int grid = 1;
+    switch (T) {
+      case 1: { auto k = sweep_ell_kernel<PT, AR, 1>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
+        k<<<grid, 256, smem, st>>>(p); break; }
+      case 2: { auto k = sweep_ell_kernel<PT, AR, 2>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
+        k<<<grid, 256, smem, st>>>(p); break; }
+      case 4: { auto k = sweep_ell_kernel<PT, AR, 4>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
+        k<<<grid, 256, smem, st>>>(p); break; }
+      case 8: { auto k = sweep_ell_kernel<PT, AR, 8>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
+        k<<<grid, 256, smem, st>>>(p); break; }
+      default: return MDP_EINVAL;
+    }
+  }
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+}  // namespace
+
+int launch_sweep(const SweepLaunch& L, cudaStream_t st) {
+  if (L.arith == 1) {
+    if (L.d.pdt != MDP_F32) return MDP_EINVAL;
+    return launch_typed<float, ArDF>(L, st);
+  }
+  if (L.d.pdt == MDP_F32) return launch_typed<float, ArF64>(L, st);
+  return launch_typed<double, ArF64>(L, st);
+}
+
+}  // namespace mdp

@@ -1,0 +1,68 @@
+"""The C-ABI library builds, loads without a GPU and exports every function the public
+header declares; the ctypes table matches the header (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "mdpgpu.h")
+
+
+def header_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(\w+)\s*\(", text, flags=re.M)
+    return sorted({n for n in names if n not in ("if", "while", "for", "return", "sizeof")})
+
+
+@pytest.fixture(scope="module")
+def built():
+    from paper_2211_04299_gb300 import build
+    return build.build()
+
+
+def test_header_lists_the_expected_entry_points():
+    names = header_functions()
+    for must in ["mdp_create_dense", "mdp_create_ell", "bellman_apply", "policy_eval_gmres",
+                 "ipi_solve", "vi_solve", "pi_solve", "opi_solve", "mdp_destroy"]:
+        assert must in names
+
+
+def test_library_exports_every_header_symbol(built):
+    lib = ctypes.CDLL(built)
+    missing = [n for n in header_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_ctypes_table_matches_header(built):
+    from paper_2211_04299_gb300 import _lib
+    assert sorted(_lib.SIGNATURES) == header_functions()
+    lib = _lib.load(built)
+    assert lib.mdp_version().decode().startswith("mdpgpu")
+    o = lib.mdp_opts_default()
+    assert o.restart == 30 and abs(o.alpha - 0.1) < 1e-15 and o.precision == 1
+
+
+def test_invalid_arguments_fail_before_any_device_work(built):
+    """Argument checks happen on the host before the CUDA runtime is touched."""
+    from paper_2211_04299_gb300 import _lib
+    lib = _lib.load(built)
+    h = ctypes.c_void_p()
+    assert lib.mdp_create_dense(0, 1, None, 0, None, 0.9, None, ctypes.byref(h)) == _lib.MDP_EINVAL
+    assert b"S must be" in lib.mdp_last_error()
+    assert lib.mdp_create_ell(4, 1, 9, None, None, 0, None, 0.9, None, ctypes.byref(h)) == _lib.MDP_EINVAL
+    assert lib.mdp_create_ell(4, 1, 2, None, None, 0, None, 1.5, None, ctypes.byref(h)) == _lib.MDP_EINVAL
+    assert lib.ipi_solve(None, None, None, None, None) == _lib.MDP_EINVAL
+
+
+def test_no_cpu_fallback_when_library_missing(tmp_path):
+    from paper_2211_04299_gb300 import _lib
+    saved = _lib._LIB
+    _lib._LIB = None
+    try:
+        with pytest.raises(ImportError):
+            _lib.load(str(tmp_path / "libmdpgpu.so"))
+    finally:
+        _lib._LIB = saved
