@@ -56,7 +56,8 @@ enum mdp_precision { MDP_PREC_FP64 = 0, MDP_PREC_MIXED = 1 };
 /* ---------------------------------------------------------------------------- handles */
 
 /* Dense MDP (Sec. 2).  P: A*S*S values of type p_dtype, P[a][s][s'] = p_{ss'}(a); every
- * row must be nonnegative, finite and sum to 1 within 1e-5 (F32) or 1e-12 (F64) absolute.
+ * row must be nonnegative, finite and sum to 1 within 1e-5 absolute (either dtype, so FP32
+ * rows widened to FP64 are accepted as the same MDP).
  * g: A*S finite FP64 costs, g[a][s] = g(s, a).  gamma in (0, 1).  mask: NULL (all actions
  * allowed) or S*A bytes, nonzero = allowed, with at least one allowed action per state.
  * On success *out holds a new handle.  Errors: MDP_EINVAL (bad sizes/values; nothing is
@@ -152,6 +153,34 @@ int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res
  * call waits for it when it is not NULL. */
 int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double* margin,
                       double* res_inf, int32_t precision);
+
+/* Largest S that bellman_apply_ell_noalloc_dev accepts. */
+#define MDP_NOALLOC_MAX_STATES (1 << 20)
+
+/* One Bellman sweep that allocates nothing, for callers that may not allocate memory while
+ * they run: a server or control loop that gave the whole device to its own pooling allocator
+ * at start-up (another allocator's cudaMalloc would fail or fragment that pool), or
+ * latency-critical code in which cudaMalloc/cudaFree, which can synchronise the device, would
+ * stall other streams.  The paper has no counterpart; it is a convenience of this library.
+ *   Inputs, all DEVICE pointers in the caller's layout, FP64 values: col[a][s][j] and
+ *   val[a][s][j] (A*S*k), g[a][s] (A*S), v[s] (S); every action is allowed.
+ *   Outputs (DEVICE): Tv[S], pi[S] (lowest index among exact minima) and res_inf[1] =
+ *   ||Tv - v||_inf, or NaN when some col lies outside [0, S) (that entry is skipped).
+ * Its only scratch is a fixed array in the library's device image (33 KiB, held by every GPU
+ * that loads the library until the process exits); no cudaMalloc, cudaFree or other
+ * allocating call is made.  S > MDP_NOALLOC_MAX_STATES is rejected with MDP_EINVAL before any
+ * work.  Errors are reported by the return code only (MDP_EINVAL for bad sizes or null
+ * pointers, MDP_EDEVICE for CUDA errors); mdp_last_error is not updated, since storing a
+ * message could allocate host memory.  The first call on a device looks the scratch address
+ * up (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls
+ * share the scratch, which keeps the last call's contents; each call clears the counters it
+ * needs on its own stream first, and calls whose work overlaps on the GPU (unordered streams)
+ * race on it.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream)
+ * and the call returns without waiting. */
+int bellman_apply_ell_noalloc_dev(int64_t S, int32_t A, int32_t k, const int32_t* col,
+                                  const double* val, const double* g, double gamma,
+                                  const double* v, double* Tv, int32_t* pi, double* res_inf,
+                                  void* stream);
 
 /* Inexact policy evaluation (Alg. 2 inner loop for a fixed pi): restarted GMRES(W) on
  * (I - gamma P^pi) V = g^pi from v0 (NULL = 0) until ||g^pi - (I - gamma P^pi) V||_inf <=

@@ -58,6 +58,7 @@ SIGNATURES = {
     "mdp_set_timing": (C.c_int, [_h, C.c_int]),
     "bellman_apply": (C.c_int, [_h, _vp, _vp, _vp, _vp, C.c_int32]),
     "bellman_apply_dev": (C.c_int, [_h, _vp, _vp, _vp, _vp, _vp, C.c_int32]),
+    "bellman_apply_ell_noalloc_dev": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp, _vp, _vp, _vp]),
     "policy_eval_gmres": (C.c_int, [_h, _vp, _vp, C.c_double, C.POINTER(mdp_opts), _vp, C.POINTER(mdp_stats)]),
     "policy_eval_gmres_dev": (C.c_int, [_h, _vp, _vp, C.c_double, C.POINTER(mdp_opts), _vp, C.POINTER(mdp_stats)]),
     "ipi_solve": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
