@@ -45,6 +45,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--S", type=int, default=S_,
+                    help="states of the dense workload (smaller values only for profiling)")
     return ap.parse_args()
 
 
@@ -231,7 +233,8 @@ def main():
     import paper_2211_04299_gb300 as mg
     import mdp_synth
 
-    syn = mdp_synth.config(2)
+    syn = mdp_synth.config(2) if args.S == S_ else \
+        mdp_synth.dense_dirichlet(args.S, A_, 0.1, GAMMA, mdp_synth.CONFIG_SEEDS[2])
     S, A = syn.S, syn.A
     h = mg.from_synth(syn)
     stream = torch.cuda.current_stream()
@@ -362,7 +365,9 @@ def main():
         h64.close()
         del syn64
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if args.S != S_:
+        line["config"]["workload"] += f" [profiling size S={S}]"
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.S == S_:
         import oracle
         counts = oracle_counts()
         m = oracle.from_synth(syn)

@@ -245,6 +245,7 @@ int sweep(mdp_t h, int arith, const void* v, const int32_t* pi_in, int32_t* pi_o
   L.out = out;
   L.partials = h->ws.partials;
   L.counter = h->ws.counter;
+  L.err = h->ws.flags + 8;
   int t = tic(h, pi_in ? 1 : 0);
   int r = launch_sweep(L, h->stream);
   toc(h, t);
@@ -268,6 +269,18 @@ int read_ctl(mdp_t h, HostCtl* c) {
   CK(cudaMemcpyAsync(h->ws.h_ctl, h->ws.ctl, sizeof(HostCtl), cudaMemcpyDeviceToHost, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   *c = *h->ws.h_ctl;
+  return MDP_OK;
+}
+
+// Bounded device waits that ran out raise flags[8]; report and clear it.
+int check_device_error(mdp_t h) {
+  int e = 0;
+  CK(cudaMemcpyAsync(&e, h->ws.flags + 8, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (e) {
+    cudaMemsetAsync(h->ws.flags + 8, 0, sizeof(int), h->stream);
+    return fail(MDP_ETIMEOUT, "a bounded device wait ran out (bulk-copy pipeline)");
+  }
   return MDP_OK;
 }
 
@@ -331,6 +344,7 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   M.out1 = w.w1;
   M.partials = w.partials;
   M.counter = w.counter;
+  M.err = w.flags + 8;
   MatvecLaunch C = M;  // true-residual check: r = rhs - J cand
   C.gate_mode = GM_CHECK;
   C.gate_mode2 = GM_RESTART;
@@ -467,6 +481,7 @@ int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* p
   RK(store_v(h, w.tv, v_out, arith));
   if (pi_out) CK(cudaMemcpyAsync(pi_out, w.pi, (size_t)h->d.S * 4, cudaMemcpyDefault, h->stream));
   CK(cudaStreamSynchronize(h->stream));
+  RK(check_device_error(h));
   collect_times(h, &st);
   st.status = status;
   st.launches = h->launches;
@@ -555,7 +570,7 @@ int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int 
   d.A = A;
   d.k = kind == KIND_ELL ? k : (int32_t)std::min<int64_t>(S, INT32_MAX);
   d.kp = kind == KIND_ELL ? (int32_t)round_up(k, 4) : 0;
-  d.ld = kind == KIND_DENSE ? round_up(S, 4) : 0;
+  d.ld = kind == KIND_DENSE ? round_up(S, 32) : 0;  // 128-byte aligned rows
   d.kind = kind;
   d.pdt = dt;
   d.gamma = gamma;
@@ -698,7 +713,7 @@ int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double*
     RK(read_sout(h, 0, &so));
     *res_inf = so.res_inf;
   }
-  return MDP_OK;
+  return res_inf ? check_device_error(h) : MDP_OK;
 }
 
 int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res_inf,
@@ -717,7 +732,7 @@ int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res
   SweepOut so;
   RK(read_sout(h, 0, &so));
   if (res_inf) *res_inf = so.res_inf;
-  return MDP_OK;
+  return check_device_error(h);
 }
 
 int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double target_inf,
@@ -747,6 +762,7 @@ int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double t
   RK(eval_policy(h, w.pi2, arith, target_inf, o, &st, &res));
   RK(store_v(h, w.v, v_out, arith));
   CK(cudaStreamSynchronize(h->stream));
+  RK(check_device_error(h));
   collect_times(h, &st);
   st.residual_inf = res;
   st.status = res <= target_inf ? MDP_OK : MDP_ENOCONV;

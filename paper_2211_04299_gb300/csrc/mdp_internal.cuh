@@ -1,7 +1,7 @@
 // Internal declarations shared by the CUDA translation units of libmdpgpu.
 //
 // Device data layout (chosen at upload, independent of the caller's layout):
-//   dense P : [S][A][ld]   state-major, ld = S rounded up to 4 (FP32) / 2 (FP64) elements,
+//   dense P : [S][A][ld]   state-major, ld = S rounded up to 32 elements (128-byte rows),
 //                          pad columns zero; a state's A rows are one contiguous stream.
 //   ELL     : val, col [S][A][kp], kp = k rounded up to 4; pad entries val 0, col 0.
 //   g       : [S][A] FP64, plus a double-float copy [S][A] for the mixed path.
@@ -182,6 +182,58 @@ __device__ __forceinline__ bool arrive_last(unsigned* counter) {
   return am_last;
 }
 
+// ------------------------------------------------------------------ bulk-copy pipeline
+// cp.async.bulk (TMA, untiled) global -> shared copies completing on an mbarrier, and the
+// mbarrier operations of a producer/consumer ring.  Every wait is bounded: after about a
+// second of spinning it raises *err and returns false, so a kernel never hangs the GPU.
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* b, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(b)),
+               "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
+}
+// try_wait with a suspend-time hint: the warp sleeps in hardware until the phase completes
+// (or about 20 us pass) instead of spinning through issue slots.
+__device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+      " selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_addr(b)), "r"(parity), "r"(20000u)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+  if (mbar_test(b, parity)) return true;
+  const long long t0 = clock64();
+  while (!mbar_test(b, parity)) {
+    if (clock64() - t0 > (1LL << 31)) {
+      if (err) atomicExch(err, 1);
+      return false;
+    }
+  }
+  return true;
+}
+// bytes and both addresses must be multiples of 16
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // ------------------------------------------------------------------ GMRES control block
 // Modes of the device-resident inner-solver state machine.  Each kernel of an Arnoldi step
 // runs only in the modes listed beside it and returns at once otherwise, so a whole step
@@ -251,6 +303,8 @@ struct SweepLaunch {
   unsigned* counter;
   int lanes;            // ELL lanes per row (1,2,4,8); 0 = choose
   int grid;             // 0 = choose
+  int* err;             // raised by a bounded wait that ran out (bulk-copy kernels)
+  int no_tma;           // force the register-streaming kernel
 };
 
 int launch_sweep(const SweepLaunch& L, cudaStream_t st);
@@ -279,6 +333,8 @@ struct MatvecLaunch {
   unsigned* counter;
   int lanes;
   int grid;
+  int* err;
+  int no_tma;
 };
 
 int launch_matvec(const MatvecLaunch& L, cudaStream_t st);

@@ -11,6 +11,7 @@
 #include "mdp_internal.cuh"
 
 #include <algorithm>
+#include <type_traits>
 
 namespace mdp {
 
@@ -126,12 +127,18 @@ template <class AR> struct Pick {
   }
 };
 
+__device__ __forceinline__ dfl shfl_idx_df(dfl x, int src) {
+  return {__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
+}
+
+// Per-state outputs of a sweep given v(s): pi, Tv, Phi, margin, reference residual, and the
+// running norms of Phi.
 template <class AR>
-__device__ __forceinline__ void emit_state(const SweepK& p, int64_t s, const Pick<AR>& pk,
-                                           typename AR::MaxT& mx, typename AR::R& ss) {
+__device__ __forceinline__ void emit_state_v(const SweepK& p, int64_t s, const Pick<AR>& pk,
+                                             typename AR::V vs, typename AR::MaxT& mx,
+                                             typename AR::R& ss) {
   using V = typename AR::V;
   using K = typename AR::K;
-  const V vs = AR::load_v((const V*)p.v, s);
   const typename AR::Qt phi = AR::sub(pk.best, vs);
   int a = pk.abest < 0 ? 0 : pk.abest;
   if (p.pi_in) a = p.pi_in[s];
@@ -147,6 +154,12 @@ __device__ __forceinline__ void emit_state(const SweepK& p, int64_t s, const Pic
   typename AR::R r = AR::absr(phi);
   mx = AR::mmax(mx, AR::absq(phi));
   ss += r * r;
+}
+
+template <class AR>
+__device__ __forceinline__ void emit_state(const SweepK& p, int64_t s, const Pick<AR>& pk,
+                                           typename AR::MaxT& mx, typename AR::R& ss) {
+  emit_state_v<AR>(p, s, pk, AR::load_v((const typename AR::V*)p.v, s), mx, ss);
 }
 
 template <class AR>
@@ -373,6 +386,247 @@ __global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
   finish_norms<AR>(p, mx, ss);
 }
 
+// ------------------------------------------------------------------ dense, bulk-copy pipeline
+// Warp-specialised sweep for FP32 P in double-float arithmetic, A <= 8.
+//   warp 16 (producer, one elected thread): streams each state's A row segments of TS_CW
+//            columns into a ring of NS shared-memory stages with cp.async.bulk;
+//   warps 0..15 (consumers): two columns of every stage for all A rows, against v resident in
+//            shared memory; at the end of a state each warp reduce-scatters its A partial sums
+//            and hands them over through a small mbarrier-guarded buffer;
+//   warp 17 (epilogue): prefetches g, v(s) for the next state, then combines the 16 warps'
+//            partials in a fixed order, forms Q = g + gamma * sum, the argmin and the outputs.
+// Consumers never stall on global memory; every wait is bounded.
+constexpr int TC_WARPS = 16;
+constexpr int TC_THREADS = (TC_WARPS + 2) * 32;
+constexpr int TS_PRODUCER = TC_WARPS;
+constexpr int TS_EPILOGUE = TC_WARPS + 1;
+constexpr int TS_CW = 1024;   // columns per stage = 2 per consumer thread
+constexpr int TS_RMAX = 8;
+constexpr int TS_NBUF = 8;    // partial-sum buffers between consumers and the epilogue warp
+
+struct TmaSweepLayout {
+  size_t stage_bytes, vpart, bar_off, red_off, total;
+  int ns;
+};
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// Each stage holds TS_RMAX row segments of TS_CW floats followed by the matching TS_CW
+// double-float entries of v (read from L2 with the rows, so nothing else stays resident).
+__host__ __device__ inline TmaSweepLayout tma_sweep_layout(int64_t /*ld*/, int ns) {
+  TmaSweepLayout L;
+  L.ns = ns;
+  L.vpart = (size_t)TS_RMAX * TS_CW * 4;
+  L.stage_bytes = L.vpart + (size_t)TS_CW * 8;
+  L.bar_off = (size_t)ns * L.stage_bytes;
+  // full[ns], empty[ns], done[NBUF], free[NBUF]
+  L.red_off = align_up(L.bar_off + (size_t)(2 * ns + 2 * TS_NBUF) * 8, 16);
+  L.total = align_up(L.red_off + (size_t)TS_NBUF * TC_WARPS * TS_RMAX * sizeof(dfl), 128);
+  return L;
+}
+
+// Sum 8 double-float values per lane over the warp by recursive halving: afterwards the
+// lanes with (lane & 3) == 0 hold the warp total of row ((lane>>4)&1)*4 + ((lane>>3)&1)*2 +
+// ((lane>>2)&1).  Nine double-float additions per lane instead of forty.
+__device__ __forceinline__ dfl warp_reduce_scatter8(const dfl (&a)[TS_RMAX], int lane) {
+  dfl b[4], c[2];
+  const bool u1 = lane & 16, u2 = lane & 8, u3 = lane & 4;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const dfl snd = u1 ? a[j] : a[j + 4];
+    const dfl kep = u1 ? a[j + 4] : a[j];
+    b[j] = df_add(kep, shfl_xor_df(snd, 16));
+  }
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    const dfl snd = u2 ? b[j] : b[j + 2];
+    const dfl kep = u2 ? b[j + 2] : b[j];
+    c[j] = df_add(kep, shfl_xor_df(snd, 8));
+  }
+  const dfl snd = u3 ? c[0] : c[1];
+  const dfl kep = u3 ? c[1] : c[0];
+  dfl d = df_add(kep, shfl_xor_df(snd, 4));
+  d = df_add(d, shfl_xor_df(d, 2));
+  d = df_add(d, shfl_xor_df(d, 1));
+  return d;
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p, int ns, int* err) {
+  extern __shared__ __align__(128) unsigned char sm[];
+  const DevMDP& d = p.d;
+  const int64_t ld = d.ld;
+  const TmaSweepLayout L = tma_sweep_layout(ld, ns);
+  unsigned char* stg = sm;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + L.bar_off);
+  uint64_t* empty = full + ns;
+  uint64_t* done = empty + ns;
+  uint64_t* freeb = done + TS_NBUF;
+  dfl* red = reinterpret_cast<dfl*>(sm + L.red_off);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int R = d.A;
+  const int nch = (int)((ld + TS_CW - 1) / TS_CW);
+  if (threadIdx.x == 0) {
+    for (int st = 0; st < ns; ++st) {
+      mbar_init(full + st, 1);
+      mbar_init(empty + st, TC_WARPS);
+    }
+    for (int b = 0; b < TS_NBUF; ++b) {
+      mbar_init(done + b, TC_WARPS);
+      mbar_init(freeb + b, 1);
+    }
+    mbar_fence_init();
+  }
+  __syncthreads();
+  ArDF::MaxT mx = ArDF::max0();
+  float ss = 0.f;
+  const float* P = (const float*)d.P;
+  if (warp == TS_PRODUCER) {
+    if (lane == 0) {
+      const float2* vg = (const float2*)p.v;
+      int n = 0;
+      bool ok = true;
+      for (int64_t s = blockIdx.x; s < d.S && ok; s += gridDim.x) {
+        const float* rowbase = P + (int64_t)s * d.A * ld;
+        for (int ch = 0; ch < nch; ++ch, ++n) {
+          const int st = n % ns;
+          if (!mbar_wait(empty + st, (uint32_t)(((n / ns) & 1) ^ 1), err)) { ok = false; break; }
+          const int64_t c0 = (int64_t)ch * TS_CW;
+          const int cc = (int)((ld - c0) < (int64_t)TS_CW ? (ld - c0) : (int64_t)TS_CW);
+          unsigned char* sg = stg + (size_t)st * L.stage_bytes;
+          mbar_expect_tx(full + st, (uint32_t)(R * cc * 4 + cc * 8));
+          for (int r = 0; r < R; ++r)
+            bulk_load(sg + (size_t)r * TS_CW * 4, rowbase + (int64_t)r * ld + c0, (uint32_t)cc * 4u,
+                      full + st);
+          bulk_load(sg + L.vpart, vg + c0, (uint32_t)cc * 8u, full + st);
+        }
+      }
+      // every issued copy has landed before the block can exit
+      for (int k = 1; k <= ns && n - k >= 0; ++k) {
+        const int m = n - k;
+        mbar_wait(full + (m % ns), (uint32_t)((m / ns) & 1), err);
+      }
+    }
+  } else if (warp == TS_EPILOGUE) {
+    int ri = 0;
+    int64_t s = blockIdx.x;
+    // prefetch the first state's costs, mask and v(s)
+    float2 gq = make_float2(0.f, 0.f);
+    uint8_t mk = 1;
+    float2 vs = make_float2(0.f, 0.f);
+    if (s < d.S) {
+      if (lane < R) {
+        gq = __ldg(d.gdf + s * d.A + lane);
+        if (d.mask) mk = d.mask[s * d.A + lane];
+      }
+      vs = __ldg((const float2*)p.v + s);
+    }
+    for (; s < d.S; s += gridDim.x, ++ri) {
+      const int buf = ri % TS_NBUF;
+      // next state's inputs, loaded while this state's partials are still being produced
+      const int64_t s2 = s + gridDim.x;
+      float2 gq2 = make_float2(0.f, 0.f);
+      uint8_t mk2 = 1;
+      float2 vs2 = make_float2(0.f, 0.f);
+      if (s2 < d.S) {
+        if (lane < R) {
+          gq2 = __ldg(d.gdf + s2 * d.A + lane);
+          if (d.mask) mk2 = d.mask[s2 * d.A + lane];
+        }
+        vs2 = __ldg((const float2*)p.v + s2);
+      }
+      if (!mbar_wait(done + buf, (uint32_t)((ri / TS_NBUF) & 1), err)) break;
+      dfl q = {0.f, 0.f};
+      if (lane < R) {
+        q = red[((size_t)buf * TC_WARPS + 0) * TS_RMAX + lane];
+        for (int w = 1; w < TC_WARPS; ++w) q = df_add(q, red[((size_t)buf * TC_WARPS + w) * TS_RMAX + lane]);
+        q = df_add(dfl{gq.x, gq.y}, df_mul(dfl{d.gamma_hi, d.gamma_lo}, q));
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(freeb + buf);
+      Pick<ArDF> pk;
+      pk.init();
+      const int aref = p.pi_ref ? p.pi_ref[s] : -1;
+      for (int a = 0; a < R; ++a) {
+        const dfl qa = shfl_idx_df(q, a);
+        const int ma = __shfl_sync(0xffffffffu, (int)mk, a);
+        pk.consider(a, qa, ma != 0, aref);
+      }
+      if (lane == 0) emit_state_v<ArDF>(p, s, pk, vs, mx, ss);
+      gq = gq2;
+      mk = mk2;
+      vs = vs2;
+    }
+  } else {
+    // ---------------- consumers
+    const int t = threadIdx.x;  // 0..511
+    const int col = 2 * t;
+    const int ldi = (int)ld;
+    bool ok = true;
+    int st = 0, ri = 0;
+    uint32_t ph = 0;
+    for (int64_t s = blockIdx.x; s < d.S && ok; s += gridDim.x, ++ri) {
+      AccDF acc[TS_RMAX];
+#pragma unroll
+      for (int g = 0; g < TS_RMAX; ++g) acc[g].init();
+      for (int c0 = 0, ch = 0; c0 < ldi; c0 += TS_CW, ++ch) {
+        if (!mbar_wait(full + st, ph, err)) { ok = false; break; }
+        const unsigned char* sg = stg + (size_t)st * L.stage_bytes;
+        if (col < ldi - c0) {
+          const float4 vv = *reinterpret_cast<const float4*>(sg + L.vpart + col * 8);
+          const float2 v0 = make_float2(vv.x, vv.y), v1 = make_float2(vv.z, vv.w);
+          const float* pp = reinterpret_cast<const float*>(sg) + col;
+#pragma unroll
+          for (int g = 0; g < TS_RMAX; ++g) {
+            if (g < R) {
+              const float2 pv = *reinterpret_cast<const float2*>(pp + g * TS_CW);
+              acc[g].add(pv.x, v0);
+              acc[g].add(pv.y, v1);
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(empty + st);
+        if (++st == ns) { st = 0; ph ^= 1u; }
+        if ((ch & 15) == 15) {
+#pragma unroll
+          for (int g = 0; g < TS_RMAX; ++g) acc[g].fold();
+        }
+      }
+      if (!ok) break;
+      dfl parts[TS_RMAX];
+#pragma unroll
+      for (int g = 0; g < TS_RMAX; ++g) parts[g] = acc[g].result();
+      const dfl tot = warp_reduce_scatter8(parts, lane);
+      const int buf = ri % TS_NBUF;
+      if (!mbar_wait(freeb + buf, (uint32_t)(((ri / TS_NBUF) & 1) ^ 1), err)) break;
+      if ((lane & 3) == 0) {
+        const int row = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+        red[((size_t)buf * TC_WARPS + warp) * TS_RMAX + row] = tot;
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(done + buf);
+    }
+  }
+  __syncthreads();
+  finish_norms<ArDF>(p, mx, ss);
+}
+
+size_t g_tma_sweep_smem_set = 0;
+
+// Stages that fit next to the resident v (0 = the pipeline does not apply).
+int tma_sweep_stages(int64_t ld) {
+  static int max_smem = 0;
+  if (max_smem == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+      max_smem = 48 * 1024;
+  }
+  for (int ns = 6; ns >= 3; --ns)
+    if (tma_sweep_layout(ld, ns).total <= (size_t)max_smem) return ns;
+  return 0;
+}
+
 template <class Kern>
 int grid_for(Kern k, int threads, size_t smem, int64_t work_units) {
   int per_sm = 0;
@@ -391,6 +645,21 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
            L.pi_ref, L.rref_out, L.out, L.partials, L.counter};
   const DevMDP& d = L.d;
   if (d.kind == KIND_DENSE) {
+    if constexpr (std::is_same<AR, ArDF>::value) {
+      const int ns = (L.pi_in || L.no_tma || d.A > TS_RMAX || !L.err) ? 0 : tma_sweep_stages(d.ld);
+      if (ns > 0) {
+        const size_t smem = tma_sweep_layout(d.ld, ns).total;
+        if (smem > g_tma_sweep_smem_set) {
+          if (cudaFuncSetAttribute(sweep_dense_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)smem) != cudaSuccess)
+            return MDP_EDEVICE;
+          g_tma_sweep_smem_set = smem;
+        }
+        const int grid = L.grid > 0 ? L.grid : (int)std::min<int64_t>(num_sms(), d.S);
+        sweep_dense_tma_kernel<<<grid, TC_THREADS, smem, st>>>(p, ns, L.err);
+        return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+      }
+    }
     auto k = sweep_dense_kernel<PT, AR, 8>;
     int grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, (d.S + 7) / 8);
     k<<<grid, 256, 0, st>>>(p);
