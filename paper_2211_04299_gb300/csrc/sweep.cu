@@ -411,18 +411,25 @@ struct TmaSweepLayout {
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
-// Each stage holds TS_RMAX row segments of TS_CW floats followed by the matching TS_CW
-// double-float entries of v (read from L2 with the rows, so nothing else stays resident).
+// Each stage holds TS_RMAX row segments of TS_CW floats; the consumers read their two
+// double-float entries of v from L2 into registers one stage ahead.
 __host__ __device__ inline TmaSweepLayout tma_sweep_layout(int64_t /*ld*/, int ns) {
   TmaSweepLayout L;
   L.ns = ns;
-  L.vpart = (size_t)TS_RMAX * TS_CW * 4;
-  L.stage_bytes = L.vpart + (size_t)TS_CW * 8;
+  L.vpart = 0;
+  L.stage_bytes = (size_t)TS_RMAX * TS_CW * 4;
   L.bar_off = (size_t)ns * L.stage_bytes;
   // full[ns], empty[ns], done[NBUF], free[NBUF]
   L.red_off = align_up(L.bar_off + (size_t)(2 * ns + 2 * TS_NBUF) * 8, 16);
   L.total = align_up(L.red_off + (size_t)TS_NBUF * TC_WARPS * TS_RMAX * sizeof(dfl), 128);
   return L;
+}
+
+// Double-word sum with TwoSum on the high words only (the low words are added): error about
+// 2^-48 (|x| + |y|), enough for partial sums bounded by ||v||_inf.
+__device__ __forceinline__ dfl df_add_fast(dfl x, dfl y) {
+  const dfl s = two_sum(x.hi, y.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(x.lo, y.lo)));
 }
 
 // Sum 8 double-float values per lane over the warp by recursive halving: afterwards the
@@ -435,22 +442,23 @@ __device__ __forceinline__ dfl warp_reduce_scatter8(const dfl (&a)[TS_RMAX], int
   for (int j = 0; j < 4; ++j) {
     const dfl snd = u1 ? a[j] : a[j + 4];
     const dfl kep = u1 ? a[j + 4] : a[j];
-    b[j] = df_add(kep, shfl_xor_df(snd, 16));
+    b[j] = df_add_fast(kep, shfl_xor_df(snd, 16));
   }
 #pragma unroll
   for (int j = 0; j < 2; ++j) {
     const dfl snd = u2 ? b[j] : b[j + 2];
     const dfl kep = u2 ? b[j + 2] : b[j];
-    c[j] = df_add(kep, shfl_xor_df(snd, 8));
+    c[j] = df_add_fast(kep, shfl_xor_df(snd, 8));
   }
   const dfl snd = u3 ? c[0] : c[1];
   const dfl kep = u3 ? c[1] : c[0];
-  dfl d = df_add(kep, shfl_xor_df(snd, 4));
-  d = df_add(d, shfl_xor_df(d, 2));
-  d = df_add(d, shfl_xor_df(d, 1));
+  dfl d = df_add_fast(kep, shfl_xor_df(snd, 4));
+  d = df_add_fast(d, shfl_xor_df(d, 2));
+  d = df_add_fast(d, shfl_xor_df(d, 1));
   return d;
 }
 
+template <int R>
 __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p, int ns, int* err) {
   extern __shared__ __align__(128) unsigned char sm[];
   const DevMDP& d = p.d;
@@ -463,7 +471,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
   uint64_t* freeb = done + TS_NBUF;
   dfl* red = reinterpret_cast<dfl*>(sm + L.red_off);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int R = d.A;
   const int nch = (int)((ld + TS_CW - 1) / TS_CW);
   if (threadIdx.x == 0) {
     for (int st = 0; st < ns; ++st) {
@@ -482,7 +489,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
   const float* P = (const float*)d.P;
   if (warp == TS_PRODUCER) {
     if (lane == 0) {
-      const float2* vg = (const float2*)p.v;
       int n = 0;
       bool ok = true;
       for (int64_t s = blockIdx.x; s < d.S && ok; s += gridDim.x) {
@@ -493,11 +499,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
           const int64_t c0 = (int64_t)ch * TS_CW;
           const int cc = (int)((ld - c0) < (int64_t)TS_CW ? (ld - c0) : (int64_t)TS_CW);
           unsigned char* sg = stg + (size_t)st * L.stage_bytes;
-          mbar_expect_tx(full + st, (uint32_t)(R * cc * 4 + cc * 8));
+          mbar_expect_tx(full + st, (uint32_t)(R * cc * 4));
           for (int r = 0; r < R; ++r)
             bulk_load(sg + (size_t)r * TS_CW * 4, rowbase + (int64_t)r * ld + c0, (uint32_t)cc * 4u,
                       full + st);
-          bulk_load(sg + L.vpart, vg + c0, (uint32_t)cc * 8u, full + st);
         }
       }
       // every issued copy has landed before the block can exit
@@ -558,30 +563,48 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
     }
   } else {
     // ---------------- consumers
+    // Per row a (hi, lo) pair: the hi part gathers the high halves of the exact products
+    // p*vh with TwoSum, every error term (product error, p*vl, TwoSum error) goes to lo.
+    // A thread adds 2 terms per stage and row, so up to 16 stages the lo word holds at most
+    // 32 error terms; beyond that the pair is folded into a double-word total.
     const int t = threadIdx.x;  // 0..511
     const int col = 2 * t;
     const int ldi = (int)ld;
+    const float4* vq = reinterpret_cast<const float4*>(p.v);  // two double-float entries
     bool ok = true;
     int st = 0, ri = 0;
     uint32_t ph = 0;
+    float4 vnext = col < ldi ? __ldg(vq + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t s = blockIdx.x; s < d.S && ok; s += gridDim.x, ++ri) {
-      AccDF acc[TS_RMAX];
+      float sh[R], sl[R];
+      dfl tot[R];
 #pragma unroll
-      for (int g = 0; g < TS_RMAX; ++g) acc[g].init();
+      for (int g = 0; g < R; ++g) { sh[g] = 0.f; sl[g] = 0.f; tot[g] = {0.f, 0.f}; }
       for (int c0 = 0, ch = 0; c0 < ldi; c0 += TS_CW, ++ch) {
+        const float4 vv = vnext;
+        {  // the v entries of the next stage (wrapping to the next state's first chunk)
+          const int cn = (c0 + TS_CW < ldi) ? c0 + TS_CW : 0;
+          vnext = (cn + col < ldi) ? __ldg(vq + ((cn + col) >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         if (!mbar_wait(full + st, ph, err)) { ok = false; break; }
         const unsigned char* sg = stg + (size_t)st * L.stage_bytes;
         if (col < ldi - c0) {
-          const float4 vv = *reinterpret_cast<const float4*>(sg + L.vpart + col * 8);
-          const float2 v0 = make_float2(vv.x, vv.y), v1 = make_float2(vv.z, vv.w);
           const float* pp = reinterpret_cast<const float*>(sg) + col;
 #pragma unroll
-          for (int g = 0; g < TS_RMAX; ++g) {
-            if (g < R) {
-              const float2 pv = *reinterpret_cast<const float2*>(pp + g * TS_CW);
-              acc[g].add(pv.x, v0);
-              acc[g].add(pv.y, v1);
-            }
+          for (int g = 0; g < R; ++g) {
+            const float2 pv = *reinterpret_cast<const float2*>(pp + g * TS_CW);
+            // term 1: p = pv.x, v = (vv.x, vv.y)
+            float prh = __fmul_rn(pv.x, vv.x);
+            float pre = __fmaf_rn(pv.x, vv.x, -prh);
+            dfl a = two_sum(sh[g], prh);
+            float lo = __fadd_rn(a.lo, __fmaf_rn(pv.x, vv.y, pre));
+            // term 2: p = pv.y, v = (vv.z, vv.w)
+            prh = __fmul_rn(pv.y, vv.z);
+            pre = __fmaf_rn(pv.y, vv.z, -prh);
+            dfl b = two_sum(a.hi, prh);
+            lo = __fadd_rn(lo, __fadd_rn(b.lo, __fmaf_rn(pv.y, vv.w, pre)));
+            sh[g] = b.hi;
+            sl[g] = __fadd_rn(sl[g], lo);
           }
         }
         __syncwarp();
@@ -589,19 +612,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
         if (++st == ns) { st = 0; ph ^= 1u; }
         if ((ch & 15) == 15) {
 #pragma unroll
-          for (int g = 0; g < TS_RMAX; ++g) acc[g].fold();
+          for (int g = 0; g < R; ++g) {
+            tot[g] = df_add(tot[g], two_sum(sh[g], sl[g]));
+            sh[g] = 0.f;
+            sl[g] = 0.f;
+          }
         }
       }
       if (!ok) break;
       dfl parts[TS_RMAX];
+      const bool folded = ldi > 16 * TS_CW;
 #pragma unroll
-      for (int g = 0; g < TS_RMAX; ++g) parts[g] = acc[g].result();
-      const dfl tot = warp_reduce_scatter8(parts, lane);
+      for (int g = 0; g < TS_RMAX; ++g) {
+        if (g < R) {
+          parts[g] = two_sum(sh[g], sl[g]);
+          if (folded) parts[g] = df_add(tot[g], parts[g]);
+        } else {
+          parts[g] = {0.f, 0.f};
+        }
+      }
+      const dfl wsum = warp_reduce_scatter8(parts, lane);
       const int buf = ri % TS_NBUF;
       if (!mbar_wait(freeb + buf, (uint32_t)(((ri / TS_NBUF) & 1) ^ 1), err)) break;
       if ((lane & 3) == 0) {
         const int row = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-        red[((size_t)buf * TC_WARPS + warp) * TS_RMAX + row] = tot;
+        red[((size_t)buf * TC_WARPS + warp) * TS_RMAX + row] = wsum;
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(done + buf);
@@ -622,7 +657,7 @@ int tma_sweep_stages(int64_t ld) {
     if (cudaDeviceGetAttribute(&max_smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
       max_smem = 48 * 1024;
   }
-  for (int ns = 6; ns >= 3; --ns)
+  for (int ns = 7; ns >= 3; --ns)
     if (tma_sweep_layout(ld, ns).total <= (size_t)max_smem) return ns;
   return 0;
 }
@@ -650,13 +685,26 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
       if (ns > 0) {
         const size_t smem = tma_sweep_layout(d.ld, ns).total;
         if (smem > g_tma_sweep_smem_set) {
-          if (cudaFuncSetAttribute(sweep_dense_tma_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                   (int)smem) != cudaSuccess)
-            return MDP_EDEVICE;
+          const void* ks[8] = {(const void*)sweep_dense_tma_kernel<1>, (const void*)sweep_dense_tma_kernel<2>,
+                               (const void*)sweep_dense_tma_kernel<3>, (const void*)sweep_dense_tma_kernel<4>,
+                               (const void*)sweep_dense_tma_kernel<5>, (const void*)sweep_dense_tma_kernel<6>,
+                               (const void*)sweep_dense_tma_kernel<7>, (const void*)sweep_dense_tma_kernel<8>};
+          for (const void* kf : ks)
+            if (cudaFuncSetAttribute(kf, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+              return MDP_EDEVICE;
           g_tma_sweep_smem_set = smem;
         }
         const int grid = L.grid > 0 ? L.grid : (int)std::min<int64_t>(num_sms(), d.S);
-        sweep_dense_tma_kernel<<<grid, TC_THREADS, smem, st>>>(p, ns, L.err);
+        switch (d.A) {
+          case 1: sweep_dense_tma_kernel<1><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          case 2: sweep_dense_tma_kernel<2><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          case 3: sweep_dense_tma_kernel<3><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          case 4: sweep_dense_tma_kernel<4><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          case 5: sweep_dense_tma_kernel<5><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          case 6: sweep_dense_tma_kernel<6><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          case 7: sweep_dense_tma_kernel<7><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+          default: sweep_dense_tma_kernel<8><<<grid, TC_THREADS, smem, st>>>(p, ns, L.err); break;
+        }
         return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
       }
     }

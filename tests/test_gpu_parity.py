@@ -55,7 +55,8 @@ def make(kind, S, A, k, seed, mask_frac=0.0, val_dtype=np.float64, gamma=0.9):
 CASES = [("ell", 1, 1, 1), ("ell", 3, 2, 2), ("ell", 33, 5, 7), ("ell", 257, 3, 16),
          ("ell", 1000, 4, 32), ("ell", 777, 16, 13), ("dense", 1, 3, None), ("dense", 3, 2, None),
          ("dense", 33, 5, None), ("dense", 130, 8, None), ("dense", 515, 9, None),
-         ("dense", 1000, 3, None)]
+         ("dense", 1000, 3, None), ("dense", 70, 1, None), ("dense", 1031, 4, None),
+         ("dense", 2049, 6, None), ("dense", 1500, 7, None)]
 
 
 @pytest.mark.parametrize("kind,S,A,k", CASES)
@@ -94,6 +95,22 @@ def test_bellman_device_pointers_and_margin(mg, prec):
     fin = np.isfinite(sw.margin)
     assert np.allclose(mg_cpu[fin], sw.margin[fin], rtol=1e-9, atol=1e-11)
     check_policy(pi.cpu().numpy(), sw)
+
+
+@pytest.mark.parametrize("S,A", [(16500, 2), (4100, 8)])
+def test_bellman_dense_wide_rows(mg, S, A):
+    """Rows longer than 16 pipeline stages (the accumulators fold into a double-word total)
+    and a width just past a stage boundary, FP32 Dirichlet rows as at the bench size."""
+    syn = mdp_synth.dense_dirichlet(S, A, 0.1, 0.99, seed=S + A)
+    m = oracle.from_synth(syn)
+    h = mg.from_synth(syn)
+    v = np.random.default_rng(3).normal(size=S) * 30 + 50
+    sw = oracle.bellman(m, v)
+    Tv, pi, res = mg.bellman_apply(h, v, precision="mixed")
+    assert rel_err(Tv, sw.Tv) <= 1e-12
+    assert abs(res - sw.res_inf) <= 1e-12 * max(1.0, np.max(np.abs(sw.Tv)))
+    check_policy(pi, sw)
+    h.close()
 
 
 def test_bellman_edge_cases(mg):
