@@ -39,7 +39,7 @@ int fail(int code, const std::string& msg) {
 inline int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
 struct HostCtl {  // leading fields of GmresCtl read back by the host
-  int mode, status, i, W, steps, max_steps, restarts, dsel, from_rhs, est_runs, checks, pad_;
+  int mode, status, i, W, steps, max_steps, restarts, dsel, from_rhs, est_runs, checks, loop_iters;
 };
 
 struct Workspace {
@@ -84,6 +84,13 @@ struct mdp_s {
   int timing = 0;
   size_t data_bytes = 0;
   Workspace ws;
+  // graph-resident inner GMRES loop of ipi_solve (rebuilt when its parameters change)
+  cudaGraphExec_t ig_exec = nullptr;
+  cudaStream_t cap = nullptr;
+  int ig_kt = -1, ig_W = 0, ig_steps = 0, ig_slot = -1;
+  double ig_alpha = -1.0;
+  const int32_t* ig_pi = nullptr;
+  const void* ig_ws = nullptr;
   std::vector<cudaEvent_t> ev;   // event pool (pairs)
   std::vector<int> ev_kind;      // 0 sweep, 1 matvec
   size_t ev_used = 0;
@@ -148,10 +155,11 @@ int ensure_ws(mdp_t h, int kt, int W) {
   return MDP_OK;
 }
 
+// Blocks of the tall-skinny Krylov kernels: about 256 rows per block, at most two per SM.
 int krylov_grid(mdp_t h) {
   const int64_t S = h->d.S;
-  int64_t g = (S + 1023) / 1024;
-  g = std::min<int64_t>(g, (int64_t)num_sms() * 4);
+  int64_t g = (S + 255) / 256;
+  g = std::min<int64_t>(g, (int64_t)num_sms() * 2);
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, MAX_RED_BLOCKS));
 }
 
@@ -310,6 +318,8 @@ int store_v(mdp_t h, const void* src, double* dst, int arith) {
   return MDP_OK;
 }
 
+int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st);
+
 // One inner solve (Alg. 2 inner loop) on J^pi delta = rhs (rhs already in ws.phi, its norms
 // in ws.sout[slot]), with pi in ws.pi (or pi_dev).  thr: absolute target when alpha == 0.
 // On return delta is added to ws.v.
@@ -325,9 +335,38 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   RK(launch_gmres_init(B, thr, std::sqrt((double)S), W, max_steps, w.sout + slot, alpha,
                        h->stream));
   h->launches += 1;
+  HostCtl hc{};
+  RK(read_ctl(h, &hc));
+  for (int it = 0; it <= max_steps + 1 && hc.mode != GM_DONE; ++it) {
+    RK(enqueue_step(h, pi_dev, h->stream));
+    h->launches += 6;
+    RK(read_ctl(h, &hc));
+  }
+  if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES did not reach a final state");
+  RK(launch_value_update(kt, w.v, w.d0, w.d1, w.ctl, nullptr, S, h->stream));
+  h->launches += 1;
+  if (st) {
+    st->inner += hc.steps;
+    st->restarts += hc.restarts;
+    st->matvecs += hc.steps + hc.checks;
+    const double ek2 = (double)ek;
+    st->bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, kt);
+    // CGS2: three passes over Q_0..Q_i plus w traffic, per step (i averaged over the cycle)
+    const double avg_m = std::min<double>(W, hc.steps) * 0.5 + 1.0;
+    st->bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * ek2;
+  }
+  if (status_out) *status_out = hc.status;
+  return MDP_OK;
+}
+
+// The Arnoldi step as enqueued kernels (matvec, CGS2 + Givens, estimate + candidate, true
+// check); every kernel is gated on the device-resident mode.
+int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st) {
+  Workspace& w = h->ws;
+  KrylovBufs B = kbufs(h);
   MatvecLaunch M{};
   M.d = h->d;
-  M.kt = kt;
+  M.kt = w.kt;
   M.pi = pi_dev;
   M.ctl = w.ctl;
   M.gate_mode = GM_STEP;
@@ -345,7 +384,7 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   M.partials = w.partials;
   M.counter = w.counter;
   M.err = w.flags + 8;
-  MatvecLaunch C = M;  // true-residual check: r = rhs - J cand
+  MatvecLaunch C = M;
   C.gate_mode = GM_CHECK;
   C.gate_mode2 = GM_RESTART;
   C.ctl = nullptr;
@@ -358,33 +397,99 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   C.u = w.phi;
   C.out = w.rbuf;
   C.qbase = nullptr;
-  HostCtl hc{};
-  RK(read_ctl(h, &hc));
-  for (int it = 0; it <= max_steps + 1 && hc.mode != GM_DONE; ++it) {
-    int t = tic(h, 1);
-    RK(launch_matvec(M, h->stream));
-    toc(h, t);
-    RK(launch_cgs2_givens(B, h->stream));
-    RK(launch_estimate(B, h->stream));
-    RK(launch_candidate(B, h->stream));
-    RK(launch_matvec(C, h->stream));
-    h->launches += 7;
-    RK(read_ctl(h, &hc));
+  RK(launch_matvec(M, st));
+  RK(launch_cgs2_givens(B, st));
+  RK(launch_estimate(B, st));
+  RK(launch_matvec(C, st));
+  return MDP_OK;
+}
+
+// Build the graph of one inner solve: prologue (start vector, zero correction, control
+// block), a WHILE node whose body is one Arnoldi step plus the loop-condition kernel, and the
+// value update V <- V + delta.  No host decision is needed inside.
+int build_inner_graph(mdp_t h, const int32_t* pi_dev, int slot, double alpha, int W, int max_steps) {
+  Workspace& w = h->ws;
+  if (h->ig_exec) {
+    cudaGraphExecDestroy(h->ig_exec);
+    h->ig_exec = nullptr;
   }
-  if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES did not reach a final state");
-  RK(launch_value_update(kt, w.v, w.d0, w.d1, w.ctl, nullptr, S, h->stream));
-  h->launches += 1;
-  if (st) {
-    st->inner += hc.steps;
-    st->restarts += hc.restarts;
-    st->matvecs += hc.steps + hc.checks;
-    const double ek2 = (double)ek;
-    st->bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, kt);
-    // CGS2: three passes over Q_0..Q_i plus w traffic, per step (i averaged over the cycle)
-    const double avg_m = std::min<double>(W, hc.steps) * 0.5 + 1.0;
-    st->bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * ek2;
+  if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
+  const int64_t S = h->d.S;
+  const size_t ek = w.kt ? 4 : 8;
+  KrylovBufs B = kbufs(h);
+  cudaGraph_t g = nullptr;
+  CK(cudaGraphCreate(&g, 0));
+  auto fail_graph = [&](int code) {
+    cudaStreamCaptureStatus cs;
+    if (cudaStreamIsCapturing(h->cap, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone) {
+      cudaGraph_t junk = nullptr;
+      cudaStreamEndCapture(h->cap, &junk);
+    }
+    cudaGetLastError();
+    cudaGraphDestroy(g);
+    return code;
+  };
+  if (cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "graph capture could not start"));
+  int r = MDP_OK;
+  if (cudaMemcpyAsync(w.rbuf, w.phi, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->cap) != cudaSuccess ||
+      cudaMemsetAsync(w.d0, 0, (size_t)S * ek, h->cap) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "graph prologue copy"));
+  r = launch_gmres_init(B, 0.0, std::sqrt((double)S), W, max_steps, w.sout + slot, alpha, h->cap);
+  if (r != MDP_OK) return fail_graph(r);
+  cudaStreamCaptureStatus cst;
+  cudaGraph_t capg = nullptr;
+  const cudaGraphNode_t* deps = nullptr;
+  size_t nd = 0;
+  if (cudaStreamGetCaptureInfo(h->cap, &cst, nullptr, &capg, &deps, nullptr, &nd) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "capture info"));
+  cudaGraphConditionalHandle hc;
+  if (cudaGraphConditionalHandleCreate(&hc, capg, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "conditional handle"));
+  cudaGraphNodeParams np = {};
+  np.type = cudaGraphNodeTypeConditional;
+  np.conditional.handle = hc;
+  np.conditional.type = cudaGraphCondTypeWhile;
+  np.conditional.size = 1;
+  cudaGraphNode_t cn;
+  if (cudaGraphAddNode(&cn, capg, deps, nullptr, nd, &np) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "conditional node"));
+  cudaGraph_t body = np.conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(h->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "capture dependencies"));
+  r = launch_value_update(w.kt, w.v, w.d0, w.d1, w.ctl, nullptr, S, h->cap);
+  if (r != MDP_OK) return fail_graph(r);
+  cudaGraph_t g2 = nullptr;
+  if (cudaStreamEndCapture(h->cap, &g2) != cudaSuccess) return fail_graph(fail(MDP_EDEVICE, "end capture"));
+  // loop body
+  if (cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
+    return fail_graph(fail(MDP_EDEVICE, "body capture could not start"));
+  r = enqueue_step(h, pi_dev, h->cap);
+  if (r == MDP_OK) r = launch_loop_cond(hc, w.ctl, max_steps + 8, h->cap);
+  if (r != MDP_OK) return fail_graph(r);
+  cudaGraph_t b2 = nullptr;
+  if (cudaStreamEndCapture(h->cap, &b2) != cudaSuccess) return fail_graph(fail(MDP_EDEVICE, "end body capture"));
+  if (cudaGraphInstantiate(&h->ig_exec, g, 0) != cudaSuccess) {
+    h->ig_exec = nullptr;
+    return fail_graph(fail(MDP_EDEVICE, "graph instantiate"));
   }
-  if (status_out) *status_out = hc.status;
+  cudaGraphDestroy(g);
+  h->ig_kt = w.kt;
+  h->ig_W = W;
+  h->ig_steps = max_steps;
+  h->ig_slot = slot;
+  h->ig_alpha = alpha;
+  h->ig_pi = pi_dev;
+  h->ig_ws = w.ctl;
+  return MDP_OK;
+}
+
+int launch_inner_graph(mdp_t h, const int32_t* pi_dev, int slot, double alpha, int W, int max_steps) {
+  Workspace& w = h->ws;
+  if (!h->ig_exec || h->ig_kt != w.kt || h->ig_W != W || h->ig_steps != max_steps ||
+      h->ig_slot != slot || h->ig_alpha != alpha || h->ig_pi != pi_dev || h->ig_ws != w.ctl)
+    RK(build_inner_graph(h, pi_dev, slot, alpha, W, max_steps));
+  CK(cudaGraphLaunch(h->ig_exec, h->stream));
   return MDP_OK;
 }
 
@@ -452,10 +557,27 @@ int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* p
   int status = MDP_ENOCONV;
   SweepOut so{};
   int k = 0;
+  bool inner_pending = false;
   for (k = 0; k <= o.max_outer; ++k) {
     // pi_k = GreedyPolicy(V_k), T V_k, Phi_k = T V_k - V_k and ||Phi_k||_inf
     RK(sweep(h, arith, w.v, nullptr, w.pi, w.tv, nullptr, w.phi, nullptr, w.sout, &st));
+    if (inner_pending) {
+      // statistics of the graph-resident inner solve that preceded this sweep
+      CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(HostCtl), cudaMemcpyDeviceToHost, h->stream));
+    }
     RK(read_sout(h, 0, &so));
+    if (inner_pending) {
+      const HostCtl hc = *w.h_ctl;
+      if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES loop ended without a final state");
+      st.inner += hc.steps;
+      st.restarts += hc.restarts;
+      st.matvecs += hc.steps + hc.checks;
+      st.bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, w.kt);
+      const double avg_m = std::min<double>(o.restart, hc.steps) * 0.5 + 1.0;
+      st.bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)h->d.S * (w.kt ? 4.0 : 8.0);
+      h->launches += 4 + 7 * hc.loop_iters;
+      inner_pending = false;
+    }
     if (so.res_inf <= o.tol) { status = MDP_OK; break; }
     if (k == o.max_outer) break;
     if (method == METH_VI) {
@@ -467,8 +589,8 @@ int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* p
         std::swap(w.v, w.tv);
       }
     } else if (method == METH_IPI) {
-      int gs = 0;
-      RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, &st, &gs));
+      RK(launch_inner_graph(h, w.pi, 0, o.alpha, o.restart, o.max_inner));
+      inner_pending = true;
     } else {  // PI: evaluate pi_k "exactly" (relative 10^-x of ||Phi_k||)
       const double target = so.res_inf * std::pow(10.0, -(double)o.pi_inner_tol_exp);
       double r = 0;
@@ -665,6 +787,8 @@ void mdp_destroy(mdp_t h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
+  if (h->ig_exec) cudaGraphExecDestroy(h->ig_exec);
+  if (h->cap) cudaStreamDestroy(h->cap);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
 }

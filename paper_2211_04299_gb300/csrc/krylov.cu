@@ -668,23 +668,37 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
   if (threadIdx.x == 0) givens_and_decide(c, sqrt((double)t), sizeof(KT) == 4);
 }
 
-// Cheap bound: r = sum_{j<=i} z_j Q_j + z_{i+1} w / hnext equals the residual of the
-// current iterate by the Arnoldi relation J Q_i = Q_{i+1} H (exact arithmetic).
+// Runs in the modes EST, RESTART and FINISH.  In one pass over Q_0..Q_i it forms the
+// candidate iterate delta_base + sum_{j<=i} y_j Q_j (into dbuf[1 - dsel]) and, in EST mode,
+// the cheap bound r = sum_{j<=i} z_j Q_j + z_{i+1} w / hnext, which equals the residual of the
+// candidate by the Arnoldi relation J Q_i = Q_{i+1} H (exact arithmetic).  The last block
+// decides: EST -> CHECK when ||r||_inf is within 1% of the threshold, else the next step or a
+// restart; FINISH -> DONE with the candidate as the result.
 template <class KT>
-__global__ void __launch_bounds__(RED_THREADS) estimate_kernel(KB b) {
+__global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
   GmresCtl* c = b.ctl;
-  if (*(volatile int*)&c->mode != GM_EST) return;
+  const int mode = *(volatile int*)&c->mode;
+  if (mode != GM_EST && mode != GM_RESTART && mode != GM_FINISH) return;
+  const bool est = mode == GM_EST;
   const int i = c->i;
   const KT* w = (const KT*)((i & 1) ? b.w1 : b.w0);
   const KT* Q = (const KT*)b.Q;
-  const KT zl = coef<KT>(c->z, c->zf, i + 1) * (KT)(1.0 / c->hnext);
+  const KT* base = (const KT*)(c->dsel ? b.d1 : b.d0);
+  KT* cand = (KT*)(c->dsel ? b.d0 : b.d1);
+  const KT zl = est ? coef<KT>(c->z, c->zf, i + 1) * (KT)(1.0 / c->hnext) : KT(0);
   int64_t r0, r1;
   block_rows(b.S, r0, r1);
   KT mx = 0;
   for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    KT x = zl * w[r];
-    for (int j = 0; j <= i; ++j) x = fma(coef<KT>(c->z, c->zf, j), Q[(int64_t)j * b.ldq + r], x);
-    mx = max(mx, (KT)fabs(x));
+    KT x = base[r];
+    KT e = est ? zl * w[r] : KT(0);
+    for (int j = 0; j <= i; ++j) {
+      const KT q = Q[(int64_t)j * b.ldq + r];
+      x = fma(coef<KT>(c->y, c->yf, j), q, x);
+      if (est) e = fma(coef<KT>(c->z, c->zf, j), q, e);
+    }
+    cand[r] = x;
+    mx = max(mx, (KT)fabs(e));
   }
   __shared__ KT shr[32];
   KT bm = block_max(mx, shr);
@@ -695,35 +709,16 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_kernel(KB b) {
   for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) t = max(t, __ldcg(part + bb));
   t = block_max(t, shr);
   if (threadIdx.x == 0) {
-    c->est_runs += 1;
-    c->last_inf = (double)t;
-    // a small margin keeps rounding in the estimate from skipping a true check
-    if ((double)t <= c->thr * 1.01) c->mode = GM_CHECK;
-    else advance(c);
-  }
-}
-
-// candidate = delta_base + sum_{j<=i} y_j Q_j, into dbuf[1 - dsel].
-template <class KT>
-__global__ void __launch_bounds__(RED_THREADS) candidate_kernel(KB b) {
-  GmresCtl* c = b.ctl;
-  const int mode = *(volatile int*)&c->mode;
-  if (mode != GM_CHECK && mode != GM_RESTART && mode != GM_FINISH) return;
-  const int i = c->i;
-  const KT* base = (const KT*)(c->dsel ? b.d1 : b.d0);
-  KT* cand = (KT*)(c->dsel ? b.d0 : b.d1);
-  const KT* Q = (const KT*)b.Q;
-  int64_t r0, r1;
-  block_rows(b.S, r0, r1);
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    KT x = base[r];
-    for (int j = 0; j <= i; ++j) x = fma(coef<KT>(c->y, c->yf, j), Q[(int64_t)j * b.ldq + r], x);
-    cand[r] = x;
-  }
-  if (!arrive_last(b.counter)) return;
-  if (threadIdx.x == 0 && mode == GM_FINISH) {
-    c->dsel = 1 - c->dsel;
-    c->mode = GM_DONE;
+    if (mode == GM_FINISH) {
+      c->dsel = 1 - c->dsel;
+      c->mode = GM_DONE;
+    } else if (est) {
+      c->est_runs += 1;
+      c->last_inf = (double)t;
+      // a small margin keeps rounding in the estimate from skipping a true check
+      if ((double)t <= c->thr * 1.01) c->mode = GM_CHECK;
+      else advance(c);
+    }
   }
 }
 
@@ -736,6 +731,7 @@ __global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double 
   c->restarts = 0;
   c->est_runs = 0;
   c->checks = 0;
+  c->loop_iters = 0;
   c->i = 0;
   c->dsel = 0;
   c->from_rhs = 1;
@@ -755,6 +751,12 @@ __global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double 
   } else {
     c->mode = GM_STEP;
   }
+}
+
+__global__ void gmres_loop_cond_kernel(cudaGraphConditionalHandle hc, GmresCtl* c, int cap) {
+  const int it = ++c->loop_iters;
+  const bool more = (c->mode != GM_DONE) && it < cap;
+  cudaGraphSetConditional(hc, more ? 1u : 0u);
 }
 
 // v += delta_result (delta_result = dbuf[dsel] once the solve is done)
@@ -901,21 +903,19 @@ int launch_cgs2_givens(const KrylovBufs& B, cudaStream_t st) {
 
 int launch_estimate(const KrylovBufs& B, cudaStream_t st) {
   KB b = make_kb(B);
-  if (B.kt == 1) estimate_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
-  else estimate_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
-  return ok_or_dev();
-}
-
-int launch_candidate(const KrylovBufs& B, cudaStream_t st) {
-  KB b = make_kb(B);
-  if (B.kt == 1) candidate_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
-  else candidate_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+  if (B.kt == 1) estimate_candidate_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
+  else estimate_candidate_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
   return ok_or_dev();
 }
 
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
                       const SweepOut* rhs_norms, double alpha, cudaStream_t st) {
   gmres_init_kernel<<<1, 1, 0, st>>>(B.ctl, thr, alpha, sqrtS, W, max_steps, rhs_norms);
+  return ok_or_dev();
+}
+
+int launch_loop_cond(cudaGraphConditionalHandle hc, GmresCtl* ctl, int cap, cudaStream_t st) {
+  gmres_loop_cond_kernel<<<1, 1, 0, st>>>(hc, ctl, cap);
   return ok_or_dev();
 }
 

@@ -260,7 +260,7 @@ struct GmresCtl {
   int restarts;
   int dsel;         // delta_base = dbuf[dsel], candidate = dbuf[1 - dsel]
   int from_rhs;     // step 0 of a cycle reads its start vector from rbuf (scaled by 1/beta)
-  int est_runs, checks, pad_;
+  int est_runs, checks, loop_iters;
   double thr;       // target on the inf-norm of the residual
   double sqrtS;
   double beta;      // 2-norm of the cycle's start residual
@@ -357,10 +357,12 @@ struct KrylovBufs {
 
 // One Arnoldi step after the matvec: CGS2 (two passes) + norm + Givens + mode decision.
 int launch_cgs2_givens(const KrylovBufs& B, cudaStream_t st);
-// Gated on GM_EST: ||Q_{0..i} z + z_{i+1} w / hnext||_inf, then decide CHECK or not.
+// Gated on EST/RESTART/FINISH: candidate = delta_base + Q_{0..i} y and, in EST mode, the
+// Arnoldi-relation bound ||Q_{0..i} z + z_{i+1} w / hnext||_inf that decides CHECK or not.
 int launch_estimate(const KrylovBufs& B, cudaStream_t st);
-// Gated on CHECK/RESTART/FINISH: candidate = delta_base + Q_{0..i} y.
-int launch_candidate(const KrylovBufs& B, cudaStream_t st);
+// Body-end kernel of the graph-resident inner loop: keeps the WHILE node looping while the
+// solve is not done and fewer than cap iterations have run (a hard guard on the loop).
+int launch_loop_cond(cudaGraphConditionalHandle hc, GmresCtl* ctl, int cap, cudaStream_t st);
 // Initialise the control block for a new inner solve (device side, no host copy).
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
                       const SweepOut* rhs_norms, double alpha, cudaStream_t st);
