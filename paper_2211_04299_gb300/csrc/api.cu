@@ -53,6 +53,7 @@ struct Workspace {
   void* d0 = nullptr;
   void* d1 = nullptr;
   void* phi = nullptr;
+  void* rref = nullptr;  // residual of the previous policy at the new iterate (Krylov type)
   void* v = nullptr;   // value vector (double or float2)
   void* tv = nullptr;
   double* stage64 = nullptr;
@@ -84,13 +85,15 @@ struct mdp_s {
   int timing = 0;
   size_t data_bytes = 0;
   Workspace ws;
-  // graph-resident inner GMRES loop of ipi_solve (rebuilt when its parameters change)
-  cudaGraphExec_t ig_exec = nullptr;
+  // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
+  // resumed on the exact residual found by the verifying sweep (rebuilt when parameters change)
+  struct InnerGraph {
+    cudaGraphExec_t exec = nullptr;
+    int kt = -1, W = 0, steps = 0;
+    double alpha = -1.0;
+    const void* ws = nullptr;
+  } ig[2];
   cudaStream_t cap = nullptr;
-  int ig_kt = -1, ig_W = 0, ig_steps = 0, ig_slot = -1;
-  double ig_alpha = -1.0;
-  const int32_t* ig_pi = nullptr;
-  const void* ig_ws = nullptr;
   std::vector<cudaEvent_t> ev;   // event pool (pairs)
   std::vector<int> ev_kind;      // 0 sweep, 1 matvec
   size_t ev_used = 0;
@@ -100,7 +103,7 @@ struct mdp_s {
 namespace {
 
 void free_ws(Workspace& w) {
-  void* ptrs[] = {w.Q, w.w0, w.w1, w.rbuf, w.d0, w.d1, w.phi, w.v, w.tv, w.stage64, w.pi, w.pi2,
+  void* ptrs[] = {w.Q, w.w0, w.w1, w.rbuf, w.d0, w.d1, w.phi, w.rref, w.v, w.tv, w.stage64, w.pi, w.pi2,
                   w.ctl, w.sout, w.partials, w.counter, w.flags};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -140,6 +143,7 @@ int ensure_ws(mdp_t h, int kt, int W) {
   RK(alloc0(&w.d0, vec, acc));
   RK(alloc0(&w.d1, vec, acc));
   RK(alloc0(&w.phi, vec, acc));
+  RK(alloc0(&w.rref, vec, acc));
   RK(alloc0(&w.v, (size_t)w.ldq * 8, acc));
   RK(alloc0(&w.tv, (size_t)w.ldq * 8, acc));
   RK(alloc0((void**)&w.stage64, (size_t)w.ldq * 8, acc));
@@ -239,8 +243,12 @@ double matvec_bytes(mdp_t h, int kt) {
 
 // ---------------------------------------------------------------- launch helpers
 int sweep(mdp_t h, int arith, const void* v, const int32_t* pi_in, int32_t* pi_out, void* tv_out,
-          double* tv64_out, void* phi_out, double* margin_out, SweepOut* out, mdp_stats* st) {
+          double* tv64_out, void* phi_out, double* margin_out, SweepOut* out, mdp_stats* st,
+          const int32_t* pi_ref = nullptr, void* rref_out = nullptr, SweepOut* ref_out = nullptr) {
   SweepLaunch L{};
+  L.pi_ref = pi_ref;
+  L.rref_out = rref_out;
+  L.ref_out = ref_out;
   L.d = h->d;
   L.arith = arith;
   L.v = v;
@@ -406,12 +414,17 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st) {
 
 // Build the graph of one inner solve: prologue (start vector, zero correction, control
 // block), a WHILE node whose body is one Arnoldi step plus the loop-condition kernel, and the
-// value update V <- V + delta.  No host decision is needed inside.
-int build_inner_graph(mdp_t h, const int32_t* pi_dev, int slot, double alpha, int W, int max_steps) {
+// value update V <- V + delta.  No host decision is needed inside.  Variant 0 starts from
+// Phi_k (norms in sout[0], threshold alpha ||Phi_k||_inf); variant 1 resumes from the exact
+// residual of the same policy (rref, norms in sout[2]) with the saved threshold.  Both accept
+// on the Arnoldi-relation estimate: the next Bellman sweep tests the exact residual.
+int build_inner_graph(mdp_t h, int variant, const int32_t* pi_dev, double alpha, int W,
+                      int max_steps) {
   Workspace& w = h->ws;
-  if (h->ig_exec) {
-    cudaGraphExecDestroy(h->ig_exec);
-    h->ig_exec = nullptr;
+  auto& gg = h->ig[variant];
+  if (gg.exec) {
+    cudaGraphExecDestroy(gg.exec);
+    gg.exec = nullptr;
   }
   if (!h->cap) CK(cudaStreamCreateWithFlags(&h->cap, cudaStreamNonBlocking));
   const int64_t S = h->d.S;
@@ -432,10 +445,12 @@ int build_inner_graph(mdp_t h, const int32_t* pi_dev, int slot, double alpha, in
   if (cudaStreamBeginCaptureToGraph(h->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return fail_graph(fail(MDP_EDEVICE, "graph capture could not start"));
   int r = MDP_OK;
-  if (cudaMemcpyAsync(w.rbuf, w.phi, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->cap) != cudaSuccess ||
+  const void* rhs = variant == 0 ? w.phi : w.rref;
+  if (cudaMemcpyAsync(w.rbuf, rhs, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->cap) != cudaSuccess ||
       cudaMemsetAsync(w.d0, 0, (size_t)S * ek, h->cap) != cudaSuccess)
     return fail_graph(fail(MDP_EDEVICE, "graph prologue copy"));
-  r = launch_gmres_init(B, 0.0, std::sqrt((double)S), W, max_steps, w.sout + slot, alpha, h->cap);
+  r = launch_gmres_init(B, 0.0, std::sqrt((double)S), W, max_steps, w.sout + (variant == 0 ? 0 : 2),
+                        alpha, h->cap, variant, 1);
   if (r != MDP_OK) return fail_graph(r);
   cudaStreamCaptureStatus cst;
   cudaGraph_t capg = nullptr;
@@ -469,27 +484,27 @@ int build_inner_graph(mdp_t h, const int32_t* pi_dev, int slot, double alpha, in
   if (r != MDP_OK) return fail_graph(r);
   cudaGraph_t b2 = nullptr;
   if (cudaStreamEndCapture(h->cap, &b2) != cudaSuccess) return fail_graph(fail(MDP_EDEVICE, "end body capture"));
-  if (cudaGraphInstantiate(&h->ig_exec, g, 0) != cudaSuccess) {
-    h->ig_exec = nullptr;
+  if (cudaGraphInstantiate(&gg.exec, g, 0) != cudaSuccess) {
+    gg.exec = nullptr;
     return fail_graph(fail(MDP_EDEVICE, "graph instantiate"));
   }
   cudaGraphDestroy(g);
-  h->ig_kt = w.kt;
-  h->ig_W = W;
-  h->ig_steps = max_steps;
-  h->ig_slot = slot;
-  h->ig_alpha = alpha;
-  h->ig_pi = pi_dev;
-  h->ig_ws = w.ctl;
+  gg.kt = w.kt;
+  gg.W = W;
+  gg.steps = max_steps;
+  gg.alpha = alpha;
+  gg.ws = w.ctl;
   return MDP_OK;
 }
 
-int launch_inner_graph(mdp_t h, const int32_t* pi_dev, int slot, double alpha, int W, int max_steps) {
+// The inner graphs always use ws.pi as the policy (the driver copies pi_{k} there).
+int launch_inner_graph(mdp_t h, int variant, double alpha, int W, int max_steps) {
   Workspace& w = h->ws;
-  if (!h->ig_exec || h->ig_kt != w.kt || h->ig_W != W || h->ig_steps != max_steps ||
-      h->ig_slot != slot || h->ig_alpha != alpha || h->ig_pi != pi_dev || h->ig_ws != w.ctl)
-    RK(build_inner_graph(h, pi_dev, slot, alpha, W, max_steps));
-  CK(cudaGraphLaunch(h->ig_exec, h->stream));
+  auto& gg = h->ig[variant];
+  if (!gg.exec || gg.kt != w.kt || gg.W != W || gg.steps != max_steps || gg.alpha != alpha ||
+      gg.ws != w.ctl)
+    RK(build_inner_graph(h, variant, w.pi, alpha, W, max_steps));
+  CK(cudaGraphLaunch(gg.exec, h->stream));
   return MDP_OK;
 }
 
@@ -545,6 +560,72 @@ int eval_policy(mdp_t h, const int32_t* pi_dev, int arith, double target, const 
   return MDP_OK;
 }
 
+// iGMRES-PI, Alg. 2.  Outer iteration k: the inner GMRES(W) solve of J^{pi_k} delta = Phi_k
+// runs as one graph launch and stops when the Arnoldi-relation estimate of
+// ||g^{pi_k} - J^{pi_k} V_{k+1}||_inf meets alpha ||Phi_k||_inf; the next Bellman sweep then
+// gives pi_{k+1}, Phi_{k+1} and, for the reference policy pi_k, the exact residual at V_{k+1}
+// (double-float or FP64).  If that exact residual is above the threshold, the inner solve
+// resumes from it (a restart from the current iterate) and the sweep is repeated, so the
+// stopping rule of Alg. 2 always holds on the exact residual.
+int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stats* st_user) {
+  const double t0 = now_s();
+  mdp_stats st{};
+  h->launches = 0;
+  const int arith = o.precision == MDP_PREC_MIXED ? 1 : 0;
+  RK(ensure_ws(h, arith, o.restart));
+  Workspace& w = h->ws;
+  const int64_t S = h->d.S;
+  RK(load_v(h, o.v0, arith));
+  int status = MDP_ENOCONV;
+  SweepOut so{};
+  int k = 0;
+  RK(sweep(h, arith, w.v, nullptr, w.pi, w.tv, nullptr, w.phi, nullptr, w.sout, &st));
+  RK(read_sout(h, 0, &so));
+  while (true) {
+    if (so.res_inf <= o.tol) { status = MDP_OK; break; }
+    if (k >= o.max_outer) break;
+    const double thr = o.alpha * so.res_inf;
+    RK(launch_inner_graph(h, 0, o.alpha, o.restart, o.max_inner));
+    ++k;
+    for (int rep = 0;; ++rep) {
+      RK(sweep(h, arith, w.v, nullptr, w.pi2, w.tv, nullptr, w.phi, nullptr, w.sout, &st, w.pi,
+               w.rref, w.sout + 2));
+      CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(HostCtl), cudaMemcpyDeviceToHost, h->stream));
+      CK(cudaMemcpyAsync(w.h_sout + 2, w.sout + 2, sizeof(SweepOut), cudaMemcpyDeviceToHost, h->stream));
+      RK(read_sout(h, 0, &so));
+      const HostCtl hc = *w.h_ctl;
+      const SweepOut sref = w.h_sout[2];
+      if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES loop ended without a final state");
+      st.inner += hc.steps;
+      st.restarts += hc.restarts;
+      st.matvecs += hc.steps + hc.checks;
+      st.bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, w.kt);
+      const double avg_m = std::min<double>(o.restart, hc.steps) * 0.5 + 1.0;
+      st.bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * (w.kt ? 4.0 : 8.0);
+      h->launches += 4 + 7 * hc.loop_iters;
+      // exact stopping test of Alg. 2 (breakdown or the step cap also end the inner loop)
+      if (!(sref.res_inf > thr) || hc.status == GS_BREAKDOWN || hc.status == GS_CAP || rep >= 8) break;
+      st.restarts += 1;
+      RK(launch_inner_graph(h, 1, o.alpha, o.restart, o.max_inner));
+    }
+    // pi_{k+1} = GreedyPolicy(V_{k+1}) becomes the current policy
+    CK(cudaMemcpyAsync(w.pi, w.pi2, (size_t)S * 4, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  st.outer = k;
+  st.residual_inf = so.res_inf;
+  RK(store_v(h, w.tv, v_out, arith));
+  if (pi_out) CK(cudaMemcpyAsync(pi_out, w.pi, (size_t)S * 4, cudaMemcpyDefault, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  RK(check_device_error(h));
+  collect_times(h, &st);
+  st.status = status;
+  st.launches = h->launches;
+  st.seconds = now_s() - t0;
+  if (st_user) *st_user = st;
+  if (status != MDP_OK) g_err = "iteration cap reached before ||T(v)-v||_inf <= tol";
+  return status;
+}
+
 int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* pi_out,
                mdp_stats* st_user) {
   const double t0 = now_s();
@@ -557,27 +638,10 @@ int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* p
   int status = MDP_ENOCONV;
   SweepOut so{};
   int k = 0;
-  bool inner_pending = false;
   for (k = 0; k <= o.max_outer; ++k) {
     // pi_k = GreedyPolicy(V_k), T V_k, Phi_k = T V_k - V_k and ||Phi_k||_inf
     RK(sweep(h, arith, w.v, nullptr, w.pi, w.tv, nullptr, w.phi, nullptr, w.sout, &st));
-    if (inner_pending) {
-      // statistics of the graph-resident inner solve that preceded this sweep
-      CK(cudaMemcpyAsync(w.h_ctl, w.ctl, sizeof(HostCtl), cudaMemcpyDeviceToHost, h->stream));
-    }
     RK(read_sout(h, 0, &so));
-    if (inner_pending) {
-      const HostCtl hc = *w.h_ctl;
-      if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES loop ended without a final state");
-      st.inner += hc.steps;
-      st.restarts += hc.restarts;
-      st.matvecs += hc.steps + hc.checks;
-      st.bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, w.kt);
-      const double avg_m = std::min<double>(o.restart, hc.steps) * 0.5 + 1.0;
-      st.bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)h->d.S * (w.kt ? 4.0 : 8.0);
-      h->launches += 4 + 7 * hc.loop_iters;
-      inner_pending = false;
-    }
     if (so.res_inf <= o.tol) { status = MDP_OK; break; }
     if (k == o.max_outer) break;
     if (method == METH_VI) {
@@ -588,9 +652,6 @@ int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* p
         RK(sweep(h, arith, w.v, w.pi, nullptr, w.tv, nullptr, nullptr, nullptr, w.sout + 2, &st));
         std::swap(w.v, w.tv);
       }
-    } else if (method == METH_IPI) {
-      RK(launch_inner_graph(h, w.pi, 0, o.alpha, o.restart, o.max_inner));
-      inner_pending = true;
     } else {  // PI: evaluate pi_k "exactly" (relative 10^-x of ||Phi_k||)
       const double target = so.res_inf * std::pow(10.0, -(double)o.pi_inner_tol_exp);
       double r = 0;
@@ -787,7 +848,8 @@ void mdp_destroy(mdp_t h) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
-  if (h->ig_exec) cudaGraphExecDestroy(h->ig_exec);
+  for (auto& gg : h->ig)
+    if (gg.exec) cudaGraphExecDestroy(gg.exec);
   if (h->cap) cudaStreamDestroy(h->cap);
   if (h->own) cudaStreamDestroy(h->own);
   delete h;
@@ -911,6 +973,7 @@ int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double targe
     RK(check_opts(h, o));                                                               \
     if (!v_out) return fail(MDP_EINVAL, "null v_out");                                  \
     if (method == METH_OPI && o.opi_W < 1) return fail(MDP_EINVAL, "opi_W must be >= 1");  \
+    if (method == METH_IPI) return run_ipi(h, o, v_out, pi_out, stats);                 \
     return run_solver(h, method, o, v_out, pi_out, stats);                              \
   }                                                                                     \
   int name(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out, mdp_stats* stats) { \

@@ -715,15 +715,24 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
     } else if (est) {
       c->est_runs += 1;
       c->last_inf = (double)t;
-      // a small margin keeps rounding in the estimate from skipping a true check
-      if ((double)t <= c->thr * 1.01) c->mode = GM_CHECK;
-      else advance(c);
+      if (c->accept_est && (double)t <= c->thr) {
+        // accepted on the estimate: the candidate is the result; the caller's next Bellman
+        // sweep evaluates the exact residual of this policy and resumes the solve if needed
+        c->dsel = 1 - c->dsel;
+        c->mode = GM_DONE;
+        c->status = GS_CONVERGED;
+      } else if (!c->accept_est && (double)t <= c->thr * 1.01) {
+        // a small margin keeps rounding in the estimate from skipping a true check
+        c->mode = GM_CHECK;
+      } else {
+        advance(c);
+      }
     }
   }
 }
 
 __global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double sqrtS, int W,
-                                  int max_steps, const SweepOut* rhs) {
+                                  int max_steps, const SweepOut* rhs, int resume, int accept_est) {
   c->W = W;
   c->max_steps = max_steps;
   c->sqrtS = sqrtS;
@@ -738,7 +747,14 @@ __global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double 
   c->status = GS_RUNNING;
   c->last_inf = rhs->res_inf;
   c->last_nrm2 = 0.0;
-  c->thr = alpha > 0.0 ? alpha * rhs->res_inf : thr;
+  if (resume) {
+    c->thr = c->thr_saved;
+  } else {
+    c->thr = alpha > 0.0 ? alpha * rhs->res_inf : thr;
+    c->thr_saved = c->thr;
+  }
+  c->accept_est = accept_est;
+  c->resumed = resume;
   const double beta = rhs->res_nrm2;
   c->beta = beta;
   for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
@@ -909,8 +925,10 @@ int launch_estimate(const KrylovBufs& B, cudaStream_t st) {
 }
 
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
-                      const SweepOut* rhs_norms, double alpha, cudaStream_t st) {
-  gmres_init_kernel<<<1, 1, 0, st>>>(B.ctl, thr, alpha, sqrtS, W, max_steps, rhs_norms);
+                      const SweepOut* rhs_norms, double alpha, cudaStream_t st, int resume,
+                      int accept_est) {
+  gmres_init_kernel<<<1, 1, 0, st>>>(B.ctl, thr, alpha, sqrtS, W, max_steps, rhs_norms, resume,
+                                     accept_est);
   return ok_or_dev();
 }
 

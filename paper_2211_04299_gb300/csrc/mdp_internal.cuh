@@ -269,6 +269,9 @@ struct GmresCtl {
   double xscale;    // scale of the vector the next matvec reads (1/beta or 1/hnext)
   double last_inf;  // last inf-norm computed (estimate or true residual)
   double last_nrm2;
+  double thr_saved; // threshold of the current outer iteration (kept for a resumed solve)
+  int accept_est;   // accept on the Arnoldi-relation estimate (the caller verifies exactly)
+  int resumed;
   double H[(WMAX + 1) * WMAX];  // column-major, leading dimension WMAX+1
   double cs[WMAX], sn[WMAX];
   double gv[WMAX + 1];
@@ -299,6 +302,7 @@ struct SweepLaunch {
   const int32_t* pi_ref;// optional: residual of this policy at v
   void* rref_out;       // Krylov type: g^pi_ref + gamma P^pi_ref v - v
   SweepOut* out;
+  SweepOut* ref_out;    // norms of rref_out
   void* partials;       // >= MAX_RED_BLOCKS * 4 doubles
   unsigned* counter;
   int lanes;            // ELL lanes per row (1,2,4,8); 0 = choose
@@ -364,8 +368,12 @@ int launch_estimate(const KrylovBufs& B, cudaStream_t st);
 // solve is not done and fewer than cap iterations have run (a hard guard on the loop).
 int launch_loop_cond(cudaGraphConditionalHandle hc, GmresCtl* ctl, int cap, cudaStream_t st);
 // Initialise the control block for a new inner solve (device side, no host copy).
+// resume != 0 keeps the threshold of the previous solve (ctl->thr_saved); accept_est != 0
+// ends the solve as soon as the Arnoldi-relation estimate meets the threshold, leaving the
+// exact test to the caller (the next Bellman sweep).
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
-                      const SweepOut* rhs_norms, double alpha, cudaStream_t st);
+                      const SweepOut* rhs_norms, double alpha, cudaStream_t st, int resume = 0,
+                      int accept_est = 0);
 
 // Value update v += delta (double or double-float), delta = chosen by ctl (or given).
 int launch_value_update(int kt, void* v, const void* d0, const void* d1, const GmresCtl* ctl,

@@ -105,8 +105,21 @@ struct SweepK {
   const int32_t* pi_ref;
   void* rref_out;
   SweepOut* out;
+  SweepOut* ref_out;
   void* partials;
   unsigned* counter;
+};
+
+// Running norms of Phi = Tv - v and of the reference-policy residual.
+template <class AR> struct Norms {
+  typename AR::MaxT mx, mx2;
+  typename AR::R ss, ss2;
+  __device__ __forceinline__ void init() {
+    mx = AR::max0();
+    mx2 = AR::max0();
+    ss = 0;
+    ss2 = 0;
+  }
 };
 
 // Running argmin over the actions of one state, lowest index on exact ties.
@@ -131,12 +144,11 @@ __device__ __forceinline__ dfl shfl_idx_df(dfl x, int src) {
   return {__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
 }
 
-// Per-state outputs of a sweep given v(s): pi, Tv, Phi, margin, reference residual, and the
-// running norms of Phi.
+// Per-state outputs of a sweep given v(s): pi, Tv, Phi, margin, the residual of the
+// reference policy (g(s, pi_ref(s)) + gamma p_s.(pi_ref(s)) v - v(s)), and running norms.
 template <class AR>
 __device__ __forceinline__ void emit_state_v(const SweepK& p, int64_t s, const Pick<AR>& pk,
-                                             typename AR::V vs, typename AR::MaxT& mx,
-                                             typename AR::R& ss) {
+                                             typename AR::V vs, Norms<AR>& nm) {
   using V = typename AR::V;
   using K = typename AR::K;
   const typename AR::Qt phi = AR::sub(pk.best, vs);
@@ -150,16 +162,22 @@ __device__ __forceinline__ void emit_state_v(const SweepK& p, int64_t s, const P
     double m = AR::to_d(pk.second);
     p.margin_out[s] = isinf(m) ? m : AR::to_d(AR::subq(pk.second, pk.best));
   }
-  if (p.rref_out) ((K*)p.rref_out)[s] = AR::to_k(AR::sub(pk.qref, vs));
-  typename AR::R r = AR::absr(phi);
-  mx = AR::mmax(mx, AR::absq(phi));
-  ss += r * r;
+  if (p.rref_out) {
+    const typename AR::Qt rr = AR::sub(pk.qref, vs);
+    ((K*)p.rref_out)[s] = AR::to_k(rr);
+    const typename AR::R r2 = AR::absr(rr);
+    nm.mx2 = AR::mmax(nm.mx2, AR::absq(rr));
+    nm.ss2 += r2 * r2;
+  }
+  const typename AR::R r = AR::absr(phi);
+  nm.mx = AR::mmax(nm.mx, AR::absq(phi));
+  nm.ss += r * r;
 }
 
 template <class AR>
 __device__ __forceinline__ void emit_state(const SweepK& p, int64_t s, const Pick<AR>& pk,
-                                           typename AR::MaxT& mx, typename AR::R& ss) {
-  emit_state_v<AR>(p, s, pk, AR::load_v((const typename AR::V*)p.v, s), mx, ss);
+                                           Norms<AR>& nm) {
+  emit_state_v<AR>(p, s, pk, AR::load_v((const typename AR::V*)p.v, s), nm);
 }
 
 template <class AR>
@@ -182,38 +200,60 @@ __device__ __forceinline__ typename AR::MaxT block_maxq(typename AR::MaxT x, typ
   return r;
 }
 
-// Block partial -> last block -> out->res_inf / res_nrm2.  Partials hold the block maximum
-// (MaxT) and the block sum of squares (R) in slots of 8 bytes each.
 template <class AR>
-__device__ __forceinline__ void finish_norms(const SweepK& p, typename AR::MaxT mx,
-                                             typename AR::R ss) {
+__device__ __forceinline__ typename AR::MaxT load_maxt(const typename AR::MaxT* pm, int b) {
+  if constexpr (sizeof(typename AR::MaxT) == 8 && sizeof(typename AR::R) == 8) {
+    return __ldcg((const double*)pm + b);
+  } else {
+    const float2 f = __ldcg((const float2*)pm + b);
+    return typename AR::MaxT{f.x, f.y};
+  }
+}
+
+// Block partials -> last block -> out (norms of Phi) and ref_out (norms of the reference
+// residual).  Partials: four arrays of MAX_RED_BLOCKS slots of 8 bytes.
+template <class AR>
+__device__ __forceinline__ void finish_norms(const SweepK& p, const Norms<AR>& nm) {
   using R = typename AR::R;
   using M = typename AR::MaxT;
   __shared__ M shm[32];
   __shared__ R shr[32];
-  M bm = block_maxq<AR>(mx, shm);
-  R bs = block_sum(ss, shr);
+  const M bm = block_maxq<AR>(nm.mx, shm);
+  const R bs = block_sum(nm.ss, shr);
+  const M bm2 = block_maxq<AR>(nm.mx2, shm);
+  const R bs2 = block_sum(nm.ss2, shr);
   M* pm = (M*)p.partials;
-  R* ps = (R*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 8);
+  M* pm2 = (M*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 8);
+  R* ps = (R*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 16);
+  R* ps2 = (R*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 24);
   if (threadIdx.x == 0) {
     pm[blockIdx.x] = bm;
     ps[blockIdx.x] = bs;
+    pm2[blockIdx.x] = bm2;
+    ps2[blockIdx.x] = bs2;
   }
   if (!arrive_last(p.counter)) return;
-  M m = AR::max0();
-  R t = 0;
+  M m = AR::max0(), m2 = AR::max0();
+  R t = 0, t2 = 0;
   for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
-    M x;
-    if constexpr (sizeof(M) == 8 && sizeof(R) == 8) x = __ldcg((const double*)pm + b);
-    else { float2 f = __ldcg((const float2*)pm + b); x = M{f.x, f.y}; }
-    m = AR::mmax(m, x);
+    m = AR::mmax(m, load_maxt<AR>(pm, b));
+    m2 = AR::mmax(m2, load_maxt<AR>(pm2, b));
     t += __ldcg(ps + b);
+    t2 += __ldcg(ps2 + b);
   }
   m = block_maxq<AR>(m, shm);
   t = block_sum(t, shr);
-  if (threadIdx.x == 0 && p.out) {
-    p.out->res_inf = AR::mtod(m);
-    p.out->res_nrm2 = sqrt((double)t);
+  m2 = block_maxq<AR>(m2, shm);
+  t2 = block_sum(t2, shr);
+  if (threadIdx.x == 0) {
+    if (p.out) {
+      p.out->res_inf = AR::mtod(m);
+      p.out->res_nrm2 = sqrt((double)t);
+    }
+    if (p.ref_out) {
+      p.ref_out->res_inf = AR::mtod(m2);
+      p.ref_out->res_nrm2 = sqrt((double)t2);
+    }
   }
 }
 
@@ -264,8 +304,8 @@ __global__ void __launch_bounds__(256) sweep_dense_kernel(SweepK p) {
   const int R = p.pi_in ? 1 : d.A;
   const PT* P = (const PT*)d.P;
   const V* v = (const V*)p.v;
-  typename AR::MaxT mx = AR::max0();
-  typename AR::R ss = 0;
+  Norms<AR> nm;
+  nm.init();
   for (int64_t s = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; s < d.S; s += nw) {
     Pick<AR> pk;
     pk.init();
@@ -311,9 +351,9 @@ __global__ void __launch_bounds__(256) sweep_dense_kernel(SweepK p) {
         }
       }
     }
-    if (lane == 0) emit_state<AR>(p, s, pk, mx, ss);
+    if (lane == 0) emit_state<AR>(p, s, pk, nm);
   }
-  finish_norms<AR>(p, mx, ss);
+  finish_norms<AR>(p, nm);
 }
 
 // ------------------------------------------------------------------ ELL: lane teams per row
@@ -333,8 +373,8 @@ __global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
   const int32_t* col = d.col;
   const V* v = (const V*)p.v;
   const int nvec = d.kp >> 2;
-  typename AR::MaxT mx = AR::max0();
-  typename AR::R ss = 0;
+  Norms<AR> nm;
+  nm.init();
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
     const int64_t s0 = tile * SB;
     const int ns = (int)((d.S - s0) < (int64_t)SB ? (d.S - s0) : (int64_t)SB);
@@ -379,11 +419,11 @@ __global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
         for (int a = 0; a < R; ++a)
           pk.consider(a, Qsm[st * R + a], d.mask ? d.mask[s * d.A + a] != 0 : true, aref);
       }
-      emit_state<AR>(p, s, pk, mx, ss);
+      emit_state<AR>(p, s, pk, nm);
     }
     __syncthreads();
   }
-  finish_norms<AR>(p, mx, ss);
+  finish_norms<AR>(p, nm);
 }
 
 // ------------------------------------------------------------------ dense, bulk-copy pipeline
@@ -484,8 +524,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
     mbar_fence_init();
   }
   __syncthreads();
-  ArDF::MaxT mx = ArDF::max0();
-  float ss = 0.f;
+  Norms<ArDF> nm;
+  nm.init();
   const float* P = (const float*)d.P;
   if (warp == TS_PRODUCER) {
     if (lane == 0) {
@@ -556,7 +596,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
         const int ma = __shfl_sync(0xffffffffu, (int)mk, a);
         pk.consider(a, qa, ma != 0, aref);
       }
-      if (lane == 0) emit_state_v<ArDF>(p, s, pk, vs, mx, ss);
+      if (lane == 0) emit_state_v<ArDF>(p, s, pk, vs, nm);
       gq = gq2;
       mk = mk2;
       vs = vs2;
@@ -643,7 +683,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
     }
   }
   __syncthreads();
-  finish_norms<ArDF>(p, mx, ss);
+  finish_norms<ArDF>(p, nm);
 }
 
 size_t g_tma_sweep_smem_set = 0;
@@ -677,7 +717,7 @@ int grid_for(Kern k, int threads, size_t smem, int64_t work_units) {
 template <class PT, class AR>
 int launch_typed(const SweepLaunch& L, cudaStream_t st) {
   SweepK p{L.d, L.v, L.pi_in, L.pi_out, L.tv_out, L.tv64_out, L.phi_out, L.margin_out,
-           L.pi_ref, L.rref_out, L.out, L.partials, L.counter};
+           L.pi_ref, L.rref_out, L.out, L.ref_out, L.partials, L.counter};
   const DevMDP& d = L.d;
   if (d.kind == KIND_DENSE) {
     if constexpr (std::is_same<AR, ArDF>::value) {
