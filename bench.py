@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="enqueue inner GMRES steps from the host (for profilers that cannot "
+                         "follow conditional CUDA-graph nodes)")
     ap.add_argument("--S", type=int, default=S_,
                     help="states of the dense workload (smaller values only for profiling)")
     return ap.parse_args()
@@ -239,7 +242,8 @@ def main():
     h = mg.from_synth(syn)
     stream = torch.cuda.current_stream()
     h.set_stream(stream)
-    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed")
+    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
+                flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0)
     v_out = torch.empty(S, dtype=torch.float64, device="cuda")
     pi_out = torch.empty(S, dtype=torch.int32, device="cuda")
 

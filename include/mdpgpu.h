@@ -109,11 +109,17 @@ typedef struct {
   int32_t precision;   /* enum mdp_precision */
   int32_t opi_W;       /* OPI: applications of T^pi per outer step (Sec. 2.1) */
   int32_t pi_inner_tol_exp; /* PI: relative GMRES tolerance 10^-x for "exact" evaluation */
+  int32_t flags;       /* MDP_FLAG_* bits */
   const double* v0;    /* initial V_0 (host for host calls, device for *_dev); NULL = 0 */
 } mdp_opts;
 
+/* ipi_solve runs each inner GMRES solve as one CUDA-graph launch with a device-side loop.
+ * MDP_FLAG_HOST_LOOP enqueues the same kernels step by step from the host instead (one
+ * host wait per Arnoldi step), for tools that cannot follow conditional graph nodes. */
+#define MDP_FLAG_HOST_LOOP 1
+
 /* alpha 0.1, tol 1e-8, restart 30, max_outer 100, max_inner 3000, precision MIXED,
- * opi_W 50, pi_inner_tol_exp 13, v0 NULL. */
+ * opi_W 50, pi_inner_tol_exp 13, flags 0, v0 NULL. */
 mdp_opts mdp_opts_default(void);
 
 typedef struct {

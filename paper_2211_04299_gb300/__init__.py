@@ -12,8 +12,8 @@ import ctypes as C
 import numpy as np
 
 from . import _lib
-from ._lib import (MDP_F32, MDP_F64, MDP_PREC_FP64, MDP_PREC_MIXED, MDPError,  # noqa: F401
-                   mdp_opts, mdp_stats)
+from ._lib import (MDP_F32, MDP_F64, MDP_FLAG_HOST_LOOP, MDP_PREC_FP64,  # noqa: F401
+                   MDP_PREC_MIXED, MDPError, mdp_opts, mdp_stats)
 
 __all__ = [
     "MDPHandle", "mdp_create_dense", "mdp_create_ell", "bellman_apply", "policy_eval_gmres",

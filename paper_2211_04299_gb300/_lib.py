@@ -13,6 +13,7 @@ LIB_PATH = os.path.join(HERE, "libmdpgpu.so")
 MDP_OK, MDP_EINVAL, MDP_ENOMEM, MDP_ENOCONV, MDP_EDEVICE, MDP_ETIMEOUT = 0, -1, -2, -3, -4, -5
 MDP_F32, MDP_F64 = 0, 1
 MDP_PREC_FP64, MDP_PREC_MIXED = 0, 1
+MDP_FLAG_HOST_LOOP = 1
 
 STATUS_NAMES = {0: "ok", -1: "einval", -2: "enomem", -3: "enoconv", -4: "edevice",
                 -5: "etimeout", 1: "breakdown"}
@@ -21,7 +22,7 @@ STATUS_NAMES = {0: "ok", -1: "einval", -2: "enomem", -3: "enoconv", -4: "edevice
 class mdp_opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("tol", C.c_double), ("restart", C.c_int32),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("precision", C.c_int32),
-                ("opi_W", C.c_int32), ("pi_inner_tol_exp", C.c_int32),
+                ("opi_W", C.c_int32), ("pi_inner_tol_exp", C.c_int32), ("flags", C.c_int32),
                 ("v0", C.POINTER(C.c_double))]
 
 

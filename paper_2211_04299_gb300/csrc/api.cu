@@ -332,16 +332,17 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st);
 // in ws.sout[slot]), with pi in ws.pi (or pi_dev).  thr: absolute target when alpha == 0.
 // On return delta is added to ws.v.
 int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double thr, int W,
-                int max_steps, mdp_stats* st, int* status_out) {
+                int max_steps, mdp_stats* st, int* status_out, const void* rhs = nullptr,
+                int resume = 0, int accept_est = 0) {
   Workspace& w = h->ws;
   const int kt = w.kt;
   const int64_t S = h->d.S;
   const size_t ek = kt ? 4 : 8;
   KrylovBufs B = kbufs(h);
-  CK(cudaMemcpyAsync(w.rbuf, w.phi, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(w.rbuf, rhs ? rhs : w.phi, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemsetAsync(w.d0, 0, (size_t)S * ek, h->stream));
   RK(launch_gmres_init(B, thr, std::sqrt((double)S), W, max_steps, w.sout + slot, alpha,
-                       h->stream));
+                       h->stream, resume, accept_est));
   h->launches += 1;
   HostCtl hc{};
   RK(read_ctl(h, &hc));
@@ -585,7 +586,10 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
     if (so.res_inf <= o.tol) { status = MDP_OK; break; }
     if (k >= o.max_outer) break;
     const double thr = o.alpha * so.res_inf;
-    RK(launch_inner_graph(h, 0, o.alpha, o.restart, o.max_inner));
+    const bool host_loop = (o.flags & MDP_FLAG_HOST_LOOP) != 0;
+    if (host_loop) RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, nullptr, nullptr,
+                                  w.phi, 0, 1));
+    else RK(launch_inner_graph(h, 0, o.alpha, o.restart, o.max_inner));
     ++k;
     for (int rep = 0;; ++rep) {
       RK(sweep(h, arith, w.v, nullptr, w.pi2, w.tv, nullptr, w.phi, nullptr, w.sout, &st, w.pi,
@@ -602,11 +606,13 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
       st.bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, w.kt);
       const double avg_m = std::min<double>(o.restart, hc.steps) * 0.5 + 1.0;
       st.bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * (w.kt ? 4.0 : 8.0);
-      h->launches += 4 + 7 * hc.loop_iters;
+      h->launches += host_loop ? 0 : 4 + 7 * hc.loop_iters;
       // exact stopping test of Alg. 2 (breakdown or the step cap also end the inner loop)
       if (!(sref.res_inf > thr) || hc.status == GS_BREAKDOWN || hc.status == GS_CAP || rep >= 8) break;
       st.restarts += 1;
-      RK(launch_inner_graph(h, 1, o.alpha, o.restart, o.max_inner));
+      if (host_loop) RK(inner_gmres(h, w.pi, 2, o.alpha, 0.0, o.restart, o.max_inner, nullptr,
+                                    nullptr, w.rref, 1, 1));
+      else RK(launch_inner_graph(h, 1, o.alpha, o.restart, o.max_inner));
     }
     // pi_{k+1} = GreedyPolicy(V_{k+1}) becomes the current policy
     CK(cudaMemcpyAsync(w.pi, w.pi2, (size_t)S * 4, cudaMemcpyDeviceToDevice, h->stream));
@@ -803,6 +809,7 @@ mdp_opts mdp_opts_default(void) {
   o.precision = MDP_PREC_MIXED;
   o.opi_W = 50;
   o.pi_inner_tol_exp = 13;
+  o.flags = 0;
   o.v0 = nullptr;
   return o;
 }

@@ -242,6 +242,20 @@ def test_ipi_dense_dirichlet_scaled(mg, prec):
     check_policy(pi, oracle.bellman(m, ref.v))
 
 
+@pytest.mark.parametrize("kind", ["ell", "dense"])
+def test_ipi_graph_and_host_loop_agree(mg, kind):
+    """The graph-resident inner loop and the host-driven one run the same kernels in the same
+    order, so the solves agree bit for bit."""
+    syn = make(kind, 700, 5, 9, seed=41, val_dtype=np.float32, gamma=0.99)
+    h = mg.from_synth(syn)
+    v1, pi1, st1 = mg.ipi_solve(h, mg.opts(tol=1e-9, precision="mixed"))
+    v2, pi2, st2 = mg.ipi_solve(h, mg.opts(tol=1e-9, precision="mixed", flags=mg.MDP_FLAG_HOST_LOOP))
+    assert st1["status"] == 0 and st2["status"] == 0
+    np.testing.assert_array_equal(v1, v2)
+    np.testing.assert_array_equal(pi1, pi2)
+    assert st1["inner"] == st2["inner"] and st1["outer"] == st2["outer"]
+
+
 def test_warm_start_is_resume(mg):
     syn = make("ell", 500, 4, 6, seed=5)
     h = mg.from_synth(syn)
