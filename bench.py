@@ -50,6 +50,9 @@ def parse():
                          "follow conditional CUDA-graph nodes)")
     ap.add_argument("--S", type=int, default=S_,
                     help="states of the dense workload (smaller values only for profiling)")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
+                    help="workload: 2 = the paper-scale dense MDP (the benchmark), 1 = small "
+                         "ELL, 3 = S=10^6 banded ELL (for measurement of the ELL kernels)")
     return ap.parse_args()
 
 
@@ -62,15 +65,30 @@ def peaks():
         return 6800.0, "fallback"
 
 
-def sweep_algorithmic_bytes(S, A):
-    """Bytes one full Bellman sweep must move: every P_a entry (FP32), the costs as
-    double-float pairs, v read once (8 B/state) and pi, Tv, Phi written (4 + 8 + 4 B)."""
-    return A * S * S * 4 + A * S * 8 + S * 8 + S * 16
+def sweep_algorithmic_bytes(syn):
+    """Bytes one full Bellman sweep must move: every P_a entry (FP32 value, plus an int32
+    column for ELL), the costs as double-float pairs, v read once (8 B/state) and pi, Tv, Phi
+    written (4 + 8 + 4 B/state)."""
+    S, A = syn.S, syn.A
+    per_row = S * 4 if syn.kind == "dense" else syn.k * 8
+    return A * S * per_row + A * S * 8 + S * 8 + S * 16
 
 
-def matvec_algorithmic_bytes(S):
+def matvec_algorithmic_bytes(syn):
     """One P^pi matvec in FP32: row pi(s) of P_{pi(s)} per state, pi, x read, w written."""
-    return S * S * 4 + S * (4 + 4 + 4)
+    S = syn.S
+    per_row = S * 4 if syn.kind == "dense" else syn.k * 8
+    return S * per_row + S * (4 + 4 + 4)
+
+
+def workload_name(args, syn):
+    if syn.kind == "dense":
+        base = WORKLOAD
+        if syn.S != S_:
+            base += f" [profiling size S={syn.S}]"
+        return base
+    return (f"ELL MDP config {args.config}: S={syn.S}, A={syn.A}, k={syn.k}, FP32 values, "
+            f"gamma={syn.gamma}; iGMRES-PI mixed FP32/double-float, alpha=0.1, W=30, tol 1e-8")
 
 
 def source_hash():
@@ -236,8 +254,14 @@ def main():
     import paper_2211_04299_gb300 as mg
     import mdp_synth
 
-    syn = mdp_synth.config(2) if args.S == S_ else \
-        mdp_synth.dense_dirichlet(args.S, A_, 0.1, GAMMA, mdp_synth.CONFIG_SEEDS[2])
+    if args.config != 2:
+        syn = mdp_synth.config(args.config)
+        if args.config == 1:
+            syn.val = syn.val.astype(np.float32)
+    elif args.S == S_:
+        syn = mdp_synth.config(2)
+    else:
+        syn = mdp_synth.dense_dirichlet(args.S, A_, 0.1, GAMMA, mdp_synth.CONFIG_SEEDS[2])
     S, A = syn.S, syn.A
     h = mg.from_synth(syn)
     stream = torch.cuda.current_stream()
@@ -288,8 +312,8 @@ def main():
     mvs = sum(s["timed_matvecs"] for s in stats)
     mv_ms = sum(s["matvec_ms"] for s in stats) / mvs if mvs else 0.0
     peak, peak_kind = peaks()
-    sb = sweep_algorithmic_bytes(S, A)
-    mb = matvec_algorithmic_bytes(S)
+    sb = sweep_algorithmic_bytes(syn)
+    mb = matvec_algorithmic_bytes(syn)
     sweep_gbs = sb / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
     mv_gbs = mb / (mv_ms * 1e-3) / 1e9 if mv_ms > 0 else 0.0
     launches = int(sum(s["launches"] for s in stats))
@@ -302,10 +326,10 @@ def main():
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "mixed: f32 P/Krylov, double-float (2xf32) values, f64 Givens",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "S": S, "A": A, "gamma": GAMMA, "tol": TOL,
+        "config": {"workload": workload_name(args, syn), "S": S, "A": A, "gamma": syn.gamma, "tol": TOL,
                    "alpha": ALPHA, "restart": W_, "precision": "mixed",
                    "parallelism": f"replicas x{world}",
-                   "l2": "inputs larger than L2 (P is 3.2 GB, L2 129 MB); no flush"},
+                   "l2": f"inputs larger than L2 (P is {sb / 1e9:.2f} GB per sweep, L2 129 MB); no flush"},
         "converged": ok,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "per_solve": {"outer": stats[-1]["outer"], "inner": stats[-1]["inner"],
@@ -316,29 +340,36 @@ def main():
         "pi_matvec": ({"ms": mv_ms, "gbs": mv_gbs, "algorithmic_bytes": mb, "frac": mv_gbs / peak}
                       if mvs else {"ms": None, "algorithmic_bytes": mb,
                                    "note": "launched inside the CUDA graph of the inner loop"}),
-        "roofline": {"bound": "hbm", "kernel": "sweep_dense_kernel<float,ArDF,8>",
+        "roofline": {"bound": "hbm",
+                     "kernel": "sweep_dense_tma_kernel" if syn.kind == "dense" else "sweep_ell_kernel",
                      "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
                      "frac": sweep_gbs / peak, "peak_source": peak_kind,
-                     "traffic": traffic_for("sweep_dense_df_cfg2")},
+                     "traffic": traffic_for("sweep_dense_df_cfg2") if (syn.kind == "dense" and S == S_) else None},
         "gpu_launches": launches,
         "clocks": clk,
     }
 
     # end to end through the host-pointer API: upload P, g from pinned memory, solve, copy back
     if not args.no_e2e:
-        P_pin = torch.from_numpy(syn.P).pin_memory()
         g_np = np.ascontiguousarray(syn.g)
-        Pn = P_pin.numpy()
+        if syn.kind == "dense":
+            pins = [torch.from_numpy(syn.P).pin_memory()]
+            load = lambda: mg.mdp_load_dense(h, pins[0].numpy(), g_np)
+        else:
+            pins = [torch.from_numpy(np.ascontiguousarray(syn.col)).pin_memory(),
+                    torch.from_numpy(np.ascontiguousarray(syn.val)).pin_memory()]
+            load = lambda: mg.mdp_load_ell(h, pins[0].numpy(), pins[1].numpy(), g_np)
+        in_bytes = sum(int(t.numel() * t.element_size()) for t in pins) + g_np.nbytes
         v_h = np.empty(S)
         pi_h = np.empty(S, np.int32)
         e2e_steps = min(args.steps, 5)
-        mg.mdp_load_dense(h, Pn, g_np)
+        load()
         mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            mg.mdp_load_dense(h, Pn, g_np)
+            load()
             mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
@@ -346,14 +377,18 @@ def main():
         if world > 1:
             dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         line["e2e"] = {"value": world * e2e_steps / float(tt.item()), "unit": "solves/s",
-                       "h2d_bytes_per_step": int(Pn.nbytes + g_np.nbytes),
+                       "h2d_bytes_per_step": in_bytes,
                        "d2h_bytes_per_step": int(v_h.nbytes + pi_h.nbytes), "steps": e2e_steps}
-        del P_pin
+        del pins
 
     # the plain per-instance FP64 form on the same MDP (P widened exactly to FP64)
     if not args.no_fp64:
-        syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="dense",
-                                   P=syn.P.astype(np.float64))
+        if syn.kind == "dense":
+            syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="dense",
+                                       P=syn.P.astype(np.float64))
+        else:
+            syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="ell",
+                                       col=syn.col, val=syn.val.astype(np.float64))
         h64 = mg.from_synth(syn64)
         h64.set_stream(stream)
         o64 = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="fp64")
@@ -373,9 +408,7 @@ def main():
         h64.close()
         del syn64
 
-    if args.S != S_:
-        line["config"]["workload"] += f" [profiling size S={S}]"
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.S == S_:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.S == S_ and args.config == 2:
         import oracle
         counts = oracle_counts()
         m = oracle.from_synth(syn)

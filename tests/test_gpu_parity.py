@@ -293,3 +293,40 @@ def test_paper_scale_dense_mixed_sampled(mg):
         two = np.sort(q)[:2]
         if two[1] - two[0] > 1e-6:
             assert pi[s] == int(np.argmin(q))
+
+
+# ------------------------------------------------------------------ banded growth-model MDPs
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_ipi_banded_ell_scaled(mg, prec):
+    """Config-3-shaped MDP (banded columns around s + shift(a), quadratic costs) at S=6000,
+    gamma=0.999, against the oracle's PI (dense LU)."""
+    syn = mdp_synth.ell_banded(6000, 16, 32, 512, 64, 0.999, seed=1003,
+                               val_dtype=np.float32 if prec == "mixed" else np.float64)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-11)
+    h = mg.from_synth(syn)
+    tol = 1e-8 if prec == "mixed" else 1e-11
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec))
+    assert st["status"] == 0, st
+    assert rel_err(v, ref.v) <= (1e-6 if prec == "mixed" else 1e-10)
+    check_policy(pi, oracle.bellman(m, ref.v))
+
+
+def test_config3_full_size_sampled(mg):
+    """S=10^6, A=16, k=32 banded, FP32 values, gamma=0.999, mixed precision to 1e-8: the
+    oracle's Bellman step at 256 sampled states confirms |T(v)(s) - v(s)| <= gamma*1e-8 and
+    the greedy action where the margin is clear."""
+    syn = mdp_synth.config(3)
+    h = mg.from_synth(syn)
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed"))
+    assert st["status"] == 0 and st["residual_inf"] <= 1e-8, st
+    rng = np.random.default_rng(1)
+    for s in rng.choice(syn.S, 256, replace=False):
+        q = np.array([syn.g[a, s] + syn.gamma * np.dot(syn.val[a, s].astype(np.float64),
+                                                       v[syn.col[a, s]]) for a in range(syn.A)])
+        assert abs(q.min() - v[s]) <= 0.999e-8 * 1.01 + 1e-12 * abs(v[s])
+        two = np.sort(q)[:2]
+        if two[1] - two[0] > 1e-6:
+            assert pi[s] == int(np.argmin(q))
+    h.close()
