@@ -159,11 +159,11 @@ int ensure_ws(mdp_t h, int kt, int W) {
   return MDP_OK;
 }
 
-// Blocks of the tall-skinny Krylov kernels: about 256 rows per block, at most two per SM.
+// Blocks of the tall-skinny Krylov kernels: about 256 rows per block, at most four per SM.
 int krylov_grid(mdp_t h) {
   const int64_t S = h->d.S;
   int64_t g = (S + 255) / 256;
-  g = std::min<int64_t>(g, (int64_t)num_sms() * 2);
+  g = std::min<int64_t>(g, (int64_t)num_sms() * 4);
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, MAX_RED_BLOCKS));
 }
 
@@ -183,6 +183,7 @@ KrylovBufs kbufs(mdp_t h) {
   B.counter = w.counter;
   B.ctl = w.ctl;
   B.grid = krylov_grid(h);
+  B.maxm = w.W + 1;
   return B;
 }
 

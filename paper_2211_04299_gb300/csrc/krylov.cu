@@ -501,26 +501,73 @@ struct KB {
   GmresCtl* ctl;
 };
 
-__device__ __forceinline__ void block_rows(int64_t S, int64_t& r0, int64_t& r1) {
-  int64_t per = (S + gridDim.x - 1) / gridDim.x;
-  per = (per + 31) & ~int64_t(31);
-  r0 = (int64_t)blockIdx.x * per;
-  r1 = min(S, r0 + per);
+
+// Rows are processed in 16-byte vector units (4 floats or 2 doubles); every Krylov buffer is
+// padded with zeros to a multiple of 32 rows, so whole units past S contribute nothing.
+template <class KT> struct TSv;
+template <> struct TSv<float> {
+  using V = float4;
+  static constexpr int R = 4;
+  static __device__ __forceinline__ V ld(const float* p) { return *reinterpret_cast<const float4*>(p); }
+  static __device__ __forceinline__ void st(float* p, V x) { *reinterpret_cast<float4*>(p) = x; }
+  static __device__ __forceinline__ V zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  static __device__ __forceinline__ float dot(V a, V b) {
+    return fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, a.w * b.w)));
+  }
+  static __device__ __forceinline__ V axpy(float c, V x, V y) {  // y + c x
+    return make_float4(fmaf(c, x.x, y.x), fmaf(c, x.y, y.y), fmaf(c, x.z, y.z), fmaf(c, x.w, y.w));
+  }
+  static __device__ __forceinline__ float amax(V x) {
+    return fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w)));
+  }
+};
+template <> struct TSv<double> {
+  using V = double2;
+  static constexpr int R = 2;
+  static __device__ __forceinline__ V ld(const double* p) { return *reinterpret_cast<const double2*>(p); }
+  static __device__ __forceinline__ void st(double* p, V x) { *reinterpret_cast<double2*>(p) = x; }
+  static __device__ __forceinline__ V zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ double dot(V a, V b) { return fma(a.x, b.x, a.y * b.y); }
+  static __device__ __forceinline__ V axpy(double c, V x, V y) {
+    return make_double2(fma(c, x.x, y.x), fma(c, x.y, y.y));
+  }
+  static __device__ __forceinline__ double amax(V x) { return fmax(fabs(x.x), fabs(x.y)); }
+};
+
+// This block's range of vector units [u0, u1).
+template <class KT>
+__device__ __forceinline__ void block_units(int64_t S, int64_t& u0, int64_t& u1) {
+  const int64_t nu = (S + TSv<KT>::R - 1) / TSv<KT>::R;
+  const int64_t per = (nu + gridDim.x - 1) / gridDim.x;
+  u0 = (int64_t)blockIdx.x * per;
+  u1 = min(nu, u0 + per);
 }
 
-// Per-block dot products Q_j^T w over the block's rows for j < m; warp w handles columns
-// j = w, w + 8, ...; result in part[blockIdx.x * (WMAX+1) + j].
-template <class KT>
-__device__ __forceinline__ void block_dots(const KT* Q, int64_t ldq, const KT* w, int m,
-                                           int64_t r0, int64_t r1, KT* part) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int j = wid; j < m; j += nw) {
-    const KT* q = Q + (int64_t)j * ldq;
-    KT acc = 0;
-    for (int64_t r = r0 + lane; r < r1; r += 32) acc = fma(q[r], w[r], acc);
-    acc = warp_sum(acc);
-    if (lane == 0) part[(int64_t)blockIdx.x * (WMAX + 1) + j] = acc;
+// Sum acc[j] (j < m) over the block into part[blockIdx.x * (WMAX+1) + j].
+template <class KT, int MAXM>
+__device__ __forceinline__ void block_reduce_cols(KT (&acc)[MAXM], int m, KT* part) {
+  __shared__ KT red[RED_THREADS / 32][MAXM];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int j = 0; j < MAXM; ++j) {
+    if (j < m) {
+      const KT x = warp_sum(acc[j]);
+      if (lane == 0) red[wid][j] = x;
+    }
   }
+  __syncthreads();
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    KT x = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][j];
+    part[(int64_t)blockIdx.x * (WMAX + 1) + j] = x;
+  }
+}
+
+// Stage m coefficients (FP64 copy for double, FP32 copy for float) in shared memory.
+template <class KT>
+__device__ __forceinline__ void stage_coefs(KT* sh, const double* d, const float* f, int m) {
+  for (int j = threadIdx.x; j < m; j += blockDim.x) sh[j] = coef<KT>(d, f, j);
+  __syncthreads();
 }
 
 // Last block: out[j] = sum over blocks of part[b][j], j < m.
@@ -538,35 +585,61 @@ __device__ __forceinline__ void reduce_dots(const KT* part, int m, double* outd,
   }
 }
 
-template <class KT>
+// CGS2 pass 1: c1 = Q_{0..i}^T w.  Each thread keeps MAXM column accumulators (MAXM is
+// fixed by the restart length, so the loop is static) and streams its vector units of w and
+// of every Q_j once.
+template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
+  using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
   const int i = c->i, m = i + 1;
   const KT* w = (const KT*)((i & 1) ? b.w1 : b.w0);
-  int64_t r0, r1;
-  block_rows(b.S, r0, r1);
-  block_dots<KT>((const KT*)b.Q, b.ldq, w, m, r0, r1, (KT*)b.partials);
+  const KT* Q = (const KT*)b.Q;
+  int64_t u0, u1;
+  block_units<KT>(b.S, u0, u1);
+  KT acc[MAXM];
+#pragma unroll
+  for (int j = 0; j < MAXM; ++j) acc[j] = 0;
+  for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    const typename T::V wv = T::ld(w + u * T::R);
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+      if (j < m) acc[j] += T::dot(T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+  }
+  block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials);
   if (!arrive_last(b.counter)) return;
   reduce_dots<KT>((const KT*)b.partials, m, c->c1, c->c1f);
 }
 
-template <class KT>
+// CGS2 pass 1 update and pass 2 projection: w -= Q c1, then c2 = Q^T w.  The second read of
+// each Q_j unit follows the first within the same thread and is served by L1.
+template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
+  using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
   const int i = c->i, m = i + 1;
   KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
   const KT* Q = (const KT*)b.Q;
-  int64_t r0, r1;
-  block_rows(b.S, r0, r1);
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    KT x = w[r];
-    for (int j = 0; j < m; ++j) x = fma(-coef<KT>(c->c1, c->c1f, j), Q[(int64_t)j * b.ldq + r], x);
-    w[r] = x;
+  __shared__ KT cf[WMAX + 1];
+  stage_coefs<KT>(cf, c->c1, c->c1f, m);
+  int64_t u0, u1;
+  block_units<KT>(b.S, u0, u1);
+  KT acc[MAXM];
+#pragma unroll
+  for (int j = 0; j < MAXM; ++j) acc[j] = 0;
+  for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    typename T::V wv = T::ld(w + u * T::R);
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+      if (j < m) wv = T::axpy(-cf[j], T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+    T::st(w + u * T::R, wv);
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+      if (j < m) acc[j] += T::dot(T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
   }
-  __syncthreads();
-  block_dots<KT>(Q, b.ldq, w, m, r0, r1, (KT*)b.partials);
+  block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials);
   if (!arrive_last(b.counter)) return;
   reduce_dots<KT>((const KT*)b.partials, m, c->c2, c->c2f);
 }
@@ -641,21 +714,27 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
   c->mode = mode;
 }
 
-template <class KT>
+// CGS2 pass 2 update, ||w||_2 and the Givens step: w -= Q c2.
+template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
+  using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
   const int i = c->i, m = i + 1;
   KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
   const KT* Q = (const KT*)b.Q;
-  int64_t r0, r1;
-  block_rows(b.S, r0, r1);
+  __shared__ KT cf[WMAX + 1];
+  stage_coefs<KT>(cf, c->c2, c->c2f, m);
+  int64_t u0, u1;
+  block_units<KT>(b.S, u0, u1);
   KT ss = 0;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    KT x = w[r];
-    for (int j = 0; j < m; ++j) x = fma(-coef<KT>(c->c2, c->c2f, j), Q[(int64_t)j * b.ldq + r], x);
-    w[r] = x;
-    ss = fma(x, x, ss);
+  for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    typename T::V wv = T::ld(w + u * T::R);
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j)
+      if (j < m) wv = T::axpy(-cf[j], T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+    T::st(w + u * T::R, wv);
+    ss += T::dot(wv, wv);
   }
   __shared__ KT shr[32];
   KT bs = block_sum(ss, shr);
@@ -672,33 +751,43 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
 // candidate iterate delta_base + sum_{j<=i} y_j Q_j (into dbuf[1 - dsel]) and, in EST mode,
 // the cheap bound r = sum_{j<=i} z_j Q_j + z_{i+1} w / hnext, which equals the residual of the
 // candidate by the Arnoldi relation J Q_i = Q_{i+1} H (exact arithmetic).  The last block
-// decides: EST -> CHECK when ||r||_inf is within 1% of the threshold, else the next step or a
-// restart; FINISH -> DONE with the candidate as the result.
-template <class KT>
+// decides: EST -> accept (or CHECK) when ||r||_inf meets the threshold, else the next step or
+// a restart; FINISH -> DONE with the candidate as the result.
+template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
+  using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   const int mode = *(volatile int*)&c->mode;
   if (mode != GM_EST && mode != GM_RESTART && mode != GM_FINISH) return;
   const bool est = mode == GM_EST;
-  const int i = c->i;
+  const int i = c->i, m = i + 1;
   const KT* w = (const KT*)((i & 1) ? b.w1 : b.w0);
   const KT* Q = (const KT*)b.Q;
   const KT* base = (const KT*)(c->dsel ? b.d1 : b.d0);
   KT* cand = (KT*)(c->dsel ? b.d0 : b.d1);
+  __shared__ KT cy[WMAX + 1], cz[WMAX + 1];
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    cy[j] = coef<KT>(c->y, c->yf, j);
+    cz[j] = est ? coef<KT>(c->z, c->zf, j) : KT(0);
+  }
+  __syncthreads();
   const KT zl = est ? coef<KT>(c->z, c->zf, i + 1) * (KT)(1.0 / c->hnext) : KT(0);
-  int64_t r0, r1;
-  block_rows(b.S, r0, r1);
+  int64_t u0, u1;
+  block_units<KT>(b.S, u0, u1);
   KT mx = 0;
-  for (int64_t r = r0 + threadIdx.x; r < r1; r += blockDim.x) {
-    KT x = base[r];
-    KT e = est ? zl * w[r] : KT(0);
-    for (int j = 0; j <= i; ++j) {
-      const KT q = Q[(int64_t)j * b.ldq + r];
-      x = fma(coef<KT>(c->y, c->yf, j), q, x);
-      if (est) e = fma(coef<KT>(c->z, c->zf, j), q, e);
+  for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    typename T::V x = T::ld(base + u * T::R);
+    typename T::V e = est ? T::axpy(zl, T::ld(w + u * T::R), T::zero()) : T::zero();
+#pragma unroll
+    for (int j = 0; j < MAXM; ++j) {
+      if (j < m) {
+        const typename T::V q = T::ld(Q + (int64_t)j * b.ldq + u * T::R);
+        x = T::axpy(cy[j], q, x);
+        if (est) e = T::axpy(cz[j], q, e);
+      }
     }
-    cand[r] = x;
-    mx = max(mx, (KT)fabs(e));
+    T::st(cand + u * T::R, x);
+    mx = max(mx, T::amax(e));
   }
   __shared__ KT shr[32];
   KT bm = block_max(mx, shr);
@@ -903,24 +992,38 @@ int launch_matvec(const MatvecLaunch& L, cudaStream_t st) {
   return launch_mv_typed<double, double>(L, st);
 }
 
+template <class KT, int MAXM>
+void launch_cgs_typed(const KB& b, int grid, cudaStream_t st) {
+  cgs_dots_kernel<KT, MAXM><<<grid, RED_THREADS, 0, st>>>(b);
+  cgs_axpy_dots_kernel<KT, MAXM><<<grid, RED_THREADS, 0, st>>>(b);
+  cgs_axpy_norm_kernel<KT, MAXM><<<grid, RED_THREADS, 0, st>>>(b);
+}
+template <class KT>
+void launch_cgs_kt(const KB& b, int grid, int maxm, cudaStream_t st) {
+  if (maxm <= 8) launch_cgs_typed<KT, 8>(b, grid, st);
+  else if (maxm <= 16) launch_cgs_typed<KT, 16>(b, grid, st);
+  else if (maxm <= 32) launch_cgs_typed<KT, 32>(b, grid, st);
+  else launch_cgs_typed<KT, 64>(b, grid, st);
+}
+template <class KT>
+void launch_est_kt(const KB& b, int grid, int maxm, cudaStream_t st) {
+  if (maxm <= 8) estimate_candidate_kernel<KT, 8><<<grid, RED_THREADS, 0, st>>>(b);
+  else if (maxm <= 16) estimate_candidate_kernel<KT, 16><<<grid, RED_THREADS, 0, st>>>(b);
+  else if (maxm <= 32) estimate_candidate_kernel<KT, 32><<<grid, RED_THREADS, 0, st>>>(b);
+  else estimate_candidate_kernel<KT, 64><<<grid, RED_THREADS, 0, st>>>(b);
+}
+
 int launch_cgs2_givens(const KrylovBufs& B, cudaStream_t st) {
   KB b = make_kb(B);
-  if (B.kt == 1) {
-    cgs_dots_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
-    cgs_axpy_dots_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
-    cgs_axpy_norm_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
-  } else {
-    cgs_dots_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
-    cgs_axpy_dots_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
-    cgs_axpy_norm_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
-  }
+  if (B.kt == 1) launch_cgs_kt<float>(b, B.grid, B.maxm, st);
+  else launch_cgs_kt<double>(b, B.grid, B.maxm, st);
   return ok_or_dev();
 }
 
 int launch_estimate(const KrylovBufs& B, cudaStream_t st) {
   KB b = make_kb(B);
-  if (B.kt == 1) estimate_candidate_kernel<float><<<B.grid, RED_THREADS, 0, st>>>(b);
-  else estimate_candidate_kernel<double><<<B.grid, RED_THREADS, 0, st>>>(b);
+  if (B.kt == 1) launch_est_kt<float>(b, B.grid, B.maxm, st);
+  else launch_est_kt<double>(b, B.grid, B.maxm, st);
   return ok_or_dev();
 }
 

@@ -357,6 +357,7 @@ struct KrylovBufs {
   unsigned* counter;
   GmresCtl* ctl;
   int grid;
+  int maxm;       // column capacity of the tall-skinny kernels (>= restart + 1)
 };
 
 // One Arnoldi step after the matvec: CGS2 (two passes) + norm + Givens + mode decision.
