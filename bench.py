@@ -49,7 +49,8 @@ def parse():
                     help="enqueue inner GMRES steps from the host (for profilers that cannot "
                          "follow conditional CUDA-graph nodes)")
     ap.add_argument("--S", type=int, default=S_,
-                    help="states of the dense workload (smaller values only for profiling)")
+                    help="states of the dense (or, with --config 3, banded) workload; other "
+                         "values only for profiling")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
                     help="workload: 2 = the paper-scale dense MDP (the benchmark), 1 = small "
                          "ELL, 3 = S=10^6 banded ELL (for measurement of the ELL kernels)")
@@ -255,7 +256,8 @@ def main():
     import mdp_synth
 
     if args.config != 2:
-        syn = mdp_synth.config(args.config)
+        scale = 1.0 if (args.config != 3 or args.S == S_) else args.S / 1_000_000
+        syn = mdp_synth.config(args.config, scale=scale)
         if args.config == 1:
             syn.val = syn.val.astype(np.float32)
     elif args.S == S_:

@@ -140,6 +140,11 @@ typedef struct {
   int32_t reserved;
 } mdp_stats;
 
+/* Kernel shape for ELL data: lanes that share one row in the Bellman sweep and in the P^pi
+ * matvec (1, 2, 4 or 8; 0 = the library's choice).  Results do not depend on it beyond the
+ * order of floating-point additions.  Returns MDP_EINVAL for other values. */
+int mdp_set_tuning(mdp_t h, int32_t ell_lanes_sweep, int32_t ell_lanes_matvec);
+
 /* When on (nonzero), every Bellman-sweep and matvec launch is bracketed by CUDA events on
  * the handle's stream and its device time is added to mdp_stats.sweep_ms / matvec_ms. */
 int mdp_set_timing(mdp_t h, int on);

@@ -93,6 +93,9 @@ class MDPHandle:
     def set_timing(self, on: bool) -> None:
         _check(lib().mdp_set_timing(self.ptr, 1 if on else 0), "mdp_set_timing")
 
+    def set_tuning(self, ell_lanes_sweep: int = 0, ell_lanes_matvec: int = 0) -> None:
+        _check(lib().mdp_set_tuning(self.ptr, ell_lanes_sweep, ell_lanes_matvec), "mdp_set_tuning")
+
 
 def mdp_create_dense(P, g, gamma: float, mask=None) -> MDPHandle:
     """P[a, s, s'] (A, S, S) float32/float64, g[a, s] (A, S) float64, mask[s, a] uint8."""

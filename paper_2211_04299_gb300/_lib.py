@@ -57,6 +57,7 @@ SIGNATURES = {
     "mdp_device_bytes": (C.c_int64, [_h]),
     "mdp_opts_default": (mdp_opts, []),
     "mdp_set_timing": (C.c_int, [_h, C.c_int]),
+    "mdp_set_tuning": (C.c_int, [_h, C.c_int32, C.c_int32]),
     "bellman_apply": (C.c_int, [_h, _vp, _vp, _vp, _vp, C.c_int32]),
     "bellman_apply_dev": (C.c_int, [_h, _vp, _vp, _vp, _vp, _vp, C.c_int32]),
     "bellman_apply_ell_noalloc_dev": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp, _vp, _vp, _vp]),

@@ -83,6 +83,8 @@ struct mdp_s {
   cudaStream_t own = nullptr;
   int device = 0;
   int timing = 0;
+  int lanes_sweep = 0;   // ELL lanes per row (0 = library choice)
+  int lanes_matvec = 0;
   size_t data_bytes = 0;
   Workspace ws;
   // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
@@ -263,6 +265,7 @@ int sweep(mdp_t h, int arith, const void* v, const int32_t* pi_in, int32_t* pi_o
   L.partials = h->ws.partials;
   L.counter = h->ws.counter;
   L.err = h->ws.flags + 8;
+  L.lanes = h->lanes_sweep;
   int t = tic(h, pi_in ? 1 : 0);
   int r = launch_sweep(L, h->stream);
   toc(h, t);
@@ -394,6 +397,7 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st) {
   M.partials = w.partials;
   M.counter = w.counter;
   M.err = w.flags + 8;
+  M.lanes = h->lanes_matvec;
   MatvecLaunch C = M;
   C.gate_mode = GM_CHECK;
   C.gate_mode2 = GM_RESTART;
@@ -867,6 +871,20 @@ int mdp_set_stream(mdp_t h, void* stream) {
   if (!h) return fail(MDP_EINVAL, "null handle");
   CK(cudaStreamSynchronize(h->stream));
   h->stream = stream ? (cudaStream_t)stream : h->own;
+  return MDP_OK;
+}
+
+int mdp_set_tuning(mdp_t h, int32_t ell_lanes_sweep, int32_t ell_lanes_matvec) {
+  if (!h) return fail(MDP_EINVAL, "null handle");
+  auto ok = [](int x) { return x == 0 || x == 1 || x == 2 || x == 4 || x == 8; };
+  if (!ok(ell_lanes_sweep) || !ok(ell_lanes_matvec)) return fail(MDP_EINVAL, "lanes must be 0, 1, 2, 4 or 8");
+  h->lanes_sweep = ell_lanes_sweep;
+  h->lanes_matvec = ell_lanes_matvec;
+  for (auto& gg : h->ig)  // captured graphs hold the old shapes
+    if (gg.exec) {
+      cudaGraphExecDestroy(gg.exec);
+      gg.exec = nullptr;
+    }
   return MDP_OK;
 }
 

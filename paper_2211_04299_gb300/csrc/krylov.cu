@@ -172,6 +172,7 @@ __global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
   const int nvec = d.kp >> 2;
   const KT* u = (const KT*)p.u;
   const KT ca = (KT)p.a, cb = (KT)p.b, cc = (KT)p.c;
+  const uint64_t pol = l2_keep_policy();
   KT mx = 0, ss = 0;
   const int64_t nteam_total = (int64_t)gridDim.x * nteams;
   for (int64_t sb = (int64_t)blockIdx.x * nteams; sb < d.S; sb += nteam_total) {
@@ -192,10 +193,10 @@ __global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
           v0 = (KT)t0.x; v1 = (KT)t0.y; v2 = (KT)t1.x; v3 = (KT)t1.y;
         }
         int4 c4 = __ldcs(reinterpret_cast<const int4*>(d.col + base) + q);
-        acc = fma(v0, __ldg(io.x + c4.x), acc);
-        acc = fma(v1, __ldg(io.x + c4.y), acc);
-        acc = fma(v2, __ldg(io.x + c4.z), acc);
-        acc = fma(v3, __ldg(io.x + c4.w), acc);
+        acc = fma(v0, ld_keep(io.x + c4.x, pol), acc);
+        acc = fma(v1, ld_keep(io.x + c4.y, pol), acc);
+        acc = fma(v2, ld_keep(io.x + c4.z, pol), acc);
+        acc = fma(v3, ld_keep(io.x + c4.w, pol), acc);
       }
     }
 #pragma unroll
@@ -566,9 +567,14 @@ __device__ __forceinline__ void block_reduce_cols(KT (&acc)[MAXM], int m, KT* pa
 // Stage m coefficients (FP64 copy for double, FP32 copy for float) in shared memory.
 template <class KT>
 __device__ __forceinline__ void stage_coefs(KT* sh, const double* d, const float* f, int m) {
-  for (int j = threadIdx.x; j < m; j += blockDim.x) sh[j] = coef<KT>(d, f, j);
+  for (int j = threadIdx.x; j <= WMAX; j += blockDim.x) sh[j] = j < m ? coef<KT>(d, f, j) : KT(0);
   __syncthreads();
 }
+
+// Columns are processed in batches of 8 with one uniform branch per batch, so the 8 loads
+// of a batch issue back to back.  Indices past the last column are clamped to it (the
+// duplicate loads hit L1) and carry zero weight.
+constexpr int TS_BATCH = 8;
 
 // Last block: out[j] = sum over blocks of part[b][j], j < m.
 template <class KT>
@@ -604,8 +610,16 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
     const typename T::V wv = T::ld(w + u * T::R);
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-      if (j < m) acc[j] += T::dot(T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
+      if (j0 < m) {
+        typename T::V q[TS_BATCH];
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t)
+          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t) acc[j0 + t] += T::dot(q[t], wv);
+      }
+    }
   }
   block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials);
   if (!arrive_last(b.counter)) return;
@@ -632,12 +646,28 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
     typename T::V wv = T::ld(w + u * T::R);
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-      if (j < m) wv = T::axpy(-cf[j], T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
+      if (j0 < m) {
+        typename T::V q[TS_BATCH];
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t)
+          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t) wv = T::axpy(-cf[j0 + t], q[t], wv);
+      }
+    }
     T::st(w + u * T::R, wv);
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-      if (j < m) acc[j] += T::dot(T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
+      if (j0 < m) {
+        typename T::V q[TS_BATCH];
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t)
+          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t) acc[j0 + t] += T::dot(q[t], wv);
+      }
+    }
   }
   block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials);
   if (!arrive_last(b.counter)) return;
@@ -731,8 +761,16 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
     typename T::V wv = T::ld(w + u * T::R);
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j)
-      if (j < m) wv = T::axpy(-cf[j], T::ld(Q + (int64_t)j * b.ldq + u * T::R), wv);
+    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
+      if (j0 < m) {
+        typename T::V q[TS_BATCH];
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t)
+          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t) wv = T::axpy(-cf[j0 + t], q[t], wv);
+      }
+    }
     T::st(w + u * T::R, wv);
     ss += T::dot(wv, wv);
   }
@@ -766,9 +804,9 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
   const KT* base = (const KT*)(c->dsel ? b.d1 : b.d0);
   KT* cand = (KT*)(c->dsel ? b.d0 : b.d1);
   __shared__ KT cy[WMAX + 1], cz[WMAX + 1];
-  for (int j = threadIdx.x; j < m; j += blockDim.x) {
-    cy[j] = coef<KT>(c->y, c->yf, j);
-    cz[j] = est ? coef<KT>(c->z, c->zf, j) : KT(0);
+  for (int j = threadIdx.x; j <= WMAX; j += blockDim.x) {
+    cy[j] = j < m ? coef<KT>(c->y, c->yf, j) : KT(0);
+    cz[j] = (est && j < m) ? coef<KT>(c->z, c->zf, j) : KT(0);
   }
   __syncthreads();
   const KT zl = est ? coef<KT>(c->z, c->zf, i + 1) * (KT)(1.0 / c->hnext) : KT(0);
@@ -779,11 +817,17 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
     typename T::V x = T::ld(base + u * T::R);
     typename T::V e = est ? T::axpy(zl, T::ld(w + u * T::R), T::zero()) : T::zero();
 #pragma unroll
-    for (int j = 0; j < MAXM; ++j) {
-      if (j < m) {
-        const typename T::V q = T::ld(Q + (int64_t)j * b.ldq + u * T::R);
-        x = T::axpy(cy[j], q, x);
-        if (est) e = T::axpy(cz[j], q, e);
+    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
+      if (j0 < m) {
+        typename T::V q[TS_BATCH];
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t)
+          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t) {
+          x = T::axpy(cy[j0 + t], q[t], x);
+          e = T::axpy(cz[j0 + t], q[t], e);
+        }
       }
     }
     T::st(cand + u * T::R, x);

@@ -121,6 +121,31 @@ struct AccDF {
   }
 };
 
+// ------------------------------------------------------------------ L2 cache policy
+// Gathered vectors (v, x: a few MB, read many times) are loaded with an evict-last L2
+// policy so the multi-GB transition streams (evict-first, ld.cs) do not push them out.
+__device__ __forceinline__ uint64_t l2_keep_policy() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+__device__ __forceinline__ float2 ld_keep(const float2* p, uint64_t pol) {
+  float2 r;
+  asm volatile("ld.global.nc.L2::cache_hint.v2.f32 {%0, %1}, [%2], %3;"
+               : "=f"(r.x), "=f"(r.y) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ double ld_keep(const double* p, uint64_t pol) {
+  double r;
+  asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(r) : "l"(p), "l"(pol));
+  return r;
+}
+__device__ __forceinline__ float ld_keep(const float* p, uint64_t pol) {
+  float r;
+  asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(r) : "l"(p), "l"(pol));
+  return r;
+}
+
 // ------------------------------------------------------------------ small helpers
 template <typename T> __device__ __forceinline__ T warp_sum(T x) {
 #pragma unroll

@@ -29,6 +29,7 @@ struct ArF64 {
     __device__ __forceinline__ void add(double p, double v) { s = fma(p, v, s); }
     __device__ __forceinline__ void add(float p, double v) { s = fma((double)p, v, s); }
     __device__ __forceinline__ void fold() {}
+    __device__ __forceinline__ void tick2() {}
     __device__ __forceinline__ double result() { return s; }
   };
   static __device__ __forceinline__ Qt reduce_team(Qt x, int T) {
@@ -66,6 +67,9 @@ struct ArDF {
     __device__ __forceinline__ void init() { a.init(); }
     __device__ __forceinline__ void add(float p, float2 v) { a.add(p, v); }
     __device__ __forceinline__ void fold() { a.fold(); }
+    __device__ __forceinline__ void tick2() {  // called every 8 terms: fold every 32
+      if (++a.n == 4) a.fold();
+    }
     __device__ __forceinline__ dfl result() { return a.result(); }
   };
   static __device__ __forceinline__ Qt reduce_team(Qt x, int T) {
@@ -143,6 +147,18 @@ template <class AR> struct Pick {
 __device__ __forceinline__ dfl shfl_idx_df(dfl x, int src) {
   return {__shfl_sync(0xffffffffu, x.hi, src), __shfl_sync(0xffffffffu, x.lo, src)};
 }
+
+template <class AR> __device__ __forceinline__ typename AR::Qt shfl_xor_q(typename AR::Qt x, int off);
+template <> __device__ __forceinline__ double shfl_xor_q<ArF64>(double x, int off) {
+  return __shfl_xor_sync(0xffffffffu, x, off);
+}
+template <> __device__ __forceinline__ dfl shfl_xor_q<ArDF>(dfl x, int off) { return shfl_xor_df(x, off); }
+
+template <class AR> __device__ __forceinline__ typename AR::Qt shfl_q(typename AR::Qt x, int src);
+template <> __device__ __forceinline__ double shfl_q<ArF64>(double x, int src) {
+  return __shfl_sync(0xffffffffu, x, src);
+}
+template <> __device__ __forceinline__ dfl shfl_q<ArDF>(dfl x, int src) { return shfl_idx_df(x, src); }
 
 // Per-state outputs of a sweep given v(s): pi, Tv, Phi, margin, the residual of the
 // reference policy (g(s, pi_ref(s)) + gamma p_s.(pi_ref(s)) v - v(s)), and running norms.
@@ -373,6 +389,7 @@ __global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
   const int32_t* col = d.col;
   const V* v = (const V*)p.v;
   const int nvec = d.kp >> 2;
+  const uint64_t pol = l2_keep_policy();
   Norms<AR> nm;
   nm.init();
   for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
@@ -393,10 +410,10 @@ __global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
           Vec4<PT> pv;
           pv.load(val + base + 4 * q);
           int4 c4 = __ldcs(reinterpret_cast<const int4*>(col + base) + q);
-          acc.add(pv.e[0], AR::load_v(v, c4.x));
-          acc.add(pv.e[1], AR::load_v(v, c4.y));
-          acc.add(pv.e[2], AR::load_v(v, c4.z));
-          acc.add(pv.e[3], AR::load_v(v, c4.w));
+          acc.add(pv.e[0], ld_keep(v + c4.x, pol));
+          acc.add(pv.e[1], ld_keep(v + c4.y, pol));
+          acc.add(pv.e[2], ld_keep(v + c4.z, pol));
+          acc.add(pv.e[3], ld_keep(v + c4.w, pol));
           if ((++it & 7) == 0) acc.fold();
         }
       }
@@ -702,6 +719,140 @@ int tma_sweep_stages(int64_t ld) {
   return 0;
 }
 
+// ------------------------------------------------------------------ ELL, warp per state group
+// T lanes share a row.  A state's R rows are padded to Rp (a power of two) row slots; a warp
+// pass covers 32/T row slots: G = (32/T)/Rp whole states, or one state in ceil(R/(32/T))
+// passes when it does not fit.  Each lane issues all loads of a batch of vectors (values,
+// columns), then their gathers of v (L2 evict-last), then the arithmetic.  The argmin over a
+// state's rows is a butterfly over the lanes that hold them, ordered by (Q, action) so the
+// lowest action index wins exact ties; it also carries the second-best Q for the margin.
+// No shared memory and no block barrier until the final norm reduction.
+template <class AR> struct Cand {
+  typename AR::Qt q, q2;  // best and second-best Q
+  int a;                  // action of the best (INT_MAX when none)
+};
+
+template <class AR>
+__device__ __forceinline__ Cand<AR> cand_merge(const Cand<AR>& x, const Cand<AR>& y) {
+  const bool xfirst = AR::lt(x.q, y.q) || (!AR::lt(y.q, x.q) && x.a < y.a);
+  Cand<AR> r;
+  r.q = xfirst ? x.q : y.q;
+  r.a = xfirst ? x.a : y.a;
+  const typename AR::Qt loser = xfirst ? y.q : x.q;
+  typename AR::Qt s2 = AR::lt(x.q2, y.q2) ? x.q2 : y.q2;
+  r.q2 = AR::lt(loser, s2) ? loser : s2;
+  return r;
+}
+
+template <class AR>
+__device__ __forceinline__ Cand<AR> cand_shfl(const Cand<AR>& x, int off) {
+  Cand<AR> r;
+  r.q = shfl_xor_q<AR>(x.q, off);
+  r.q2 = shfl_xor_q<AR>(x.q2, off);
+  r.a = __shfl_xor_sync(0xffffffffu, x.a, off);
+  return r;
+}
+
+template <class PT, class AR, int T>
+__global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
+  using V = typename AR::V;
+  using Qt = typename AR::Qt;
+  const DevMDP& d = p.d;
+  const int lane = threadIdx.x & 31;
+  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int R = p.pi_in ? 1 : d.A;
+  constexpr int RPI = 32 / T;                  // row slots per pass
+  int Rp = 1;
+  while (Rp < R && Rp < RPI) Rp <<= 1;         // row slots of one state per pass
+  const int G = RPI / Rp;                      // states per pass
+  const int npass = (R + RPI - 1) / RPI;       // passes per state
+  const int row_slot = lane / T, tl = lane % T;
+  const int g = row_slot / Rp, rr = row_slot % Rp;
+  const int leader = g * Rp * T;
+  const PT* val = (const PT*)d.P;
+  const int32_t* col = d.col;
+  const V* v = (const V*)p.v;
+  const int nvec = d.kp >> 2;
+  const uint64_t pol = l2_keep_policy();
+  Norms<AR> nm;
+  nm.init();
+  for (int64_t s0 = gw * G; s0 < d.S; s0 += nw * G) {
+    const int64_t s = s0 + g;
+    const bool st_ok = s < d.S;
+    Cand<AR> run;
+    run.q = AR::inf(); run.q2 = AR::inf(); run.a = 0x7fffffff;
+    Qt qref = AR::inf();
+    const int aref = (p.pi_ref && st_ok) ? p.pi_ref[s] : -1;
+    for (int pass = 0; pass < npass; ++pass) {
+      const int a_local = pass * RPI + rr;
+      const bool act = st_ok && a_local < R;
+      const int a = act ? (p.pi_in ? p.pi_in[s] : a_local) : 0;
+      typename AR::Acc acc;
+      acc.init();
+      if (act) {
+        const int64_t base = ((int64_t)s * d.A + a) * d.kp;
+        for (int q0 = tl; q0 < nvec; q0 += 2 * T) {
+          Vec4<PT> pv[2];
+          int4 c4[2];
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            const int q = q0 + b * T;
+            if (q < nvec) {
+              pv[b].load(val + base + 4 * q);
+              c4[b] = __ldcs(reinterpret_cast<const int4*>(col + base) + q);
+            } else {
+              c4[b] = make_int4(0, 0, 0, 0);
+#pragma unroll
+              for (int e = 0; e < 4; ++e) pv[b].e[e] = PT(0);
+            }
+          }
+          V x[8];
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+            x[4 * b + 0] = ld_keep(v + c4[b].x, pol);
+            x[4 * b + 1] = ld_keep(v + c4[b].y, pol);
+            x[4 * b + 2] = ld_keep(v + c4[b].z, pol);
+            x[4 * b + 3] = ld_keep(v + c4[b].w, pol);
+          }
+#pragma unroll
+          for (int b = 0; b < 2; ++b) {
+#pragma unroll
+            for (int e = 0; e < 4; ++e) acc.add(pv[b].e[e], x[4 * b + e]);
+          }
+          acc.tick2();
+        }
+      }
+      const Qt sum = AR::reduce_team(acc.result(), T);
+      const Qt q = act ? AR::qval(d, s, a, sum) : AR::inf();
+      const bool allowed = act && (p.pi_in ? true : (d.mask ? d.mask[s * d.A + a] != 0 : true));
+      // reference-policy row of this pass (when it lies here): its lane holds qref.  Every
+      // lane takes part in the shuffle; only lanes whose reference row is in this pass keep it.
+      {
+        const int aoff = aref - pass * RPI;
+        const bool here = aref >= 0 && aoff >= 0 && aoff < Rp && aref < R;
+        const Qt qs = shfl_q<AR>(q, leader + (here ? aoff : 0) * T);
+        if (here) qref = qs;
+      }
+      Cand<AR> c;
+      c.q = allowed ? q : AR::inf();
+      c.q2 = AR::inf();
+      c.a = allowed ? a : 0x7fffffff;
+      for (int off = T; off < Rp * T; off <<= 1) c = cand_merge<AR>(c, cand_shfl<AR>(c, off));
+      run = cand_merge<AR>(run, c);
+    }
+    if (lane == leader && st_ok) {
+      Pick<AR> pk;
+      pk.best = run.q;
+      pk.second = run.q2;
+      pk.abest = p.pi_in ? p.pi_in[s] : (run.a == 0x7fffffff ? -1 : run.a);
+      pk.qref = qref;
+      emit_state<AR>(p, s, pk, nm);
+    }
+  }
+  finish_norms<AR>(p, nm);
+}
+
 template <class Kern>
 int grid_for(Kern k, int threads, size_t smem, int64_t work_units) {
   int per_sm = 0;
@@ -754,27 +905,24 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
   } else {
     int T = L.lanes;
     if (T <= 0) {
-      int nvec = d.kp / 4;
+      const int nvec = d.kp / 4;
       T = nvec >= 8 ? 2 : 1;
     }
-    const int R = L.pi_in ? 1 : d.A;
-    const int SB = std::max(1, (256 / T) / R);
-    const size_t smem = (size_t)SB * R * sizeof(typename AR::Qt);
-    const int64_t ntiles = (d.S + SB - 1) / SB;
+    const int64_t units = (d.S + 7) / 8;
     int grid = 1;
     switch (T) {
-      case 1: { auto k = sweep_ell_kernel<PT, AR, 1>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
-        k<<<grid, 256, smem, st>>>(p); break; }
-      case 2: { auto k = sweep_ell_kernel<PT, AR, 2>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
-        k<<<grid, 256, smem, st>>>(p); break; }
-      case 4: { auto k = sweep_ell_kernel<PT, AR, 4>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
-        k<<<grid, 256, smem, st>>>(p); break; }
-      case 8: { auto k = sweep_ell_kernel<PT, AR, 8>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, smem, ntiles);
-        k<<<grid, 256, smem, st>>>(p); break; }
+      case 1: { auto k = sweep_ell_warp_kernel<PT, AR, 1>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
+        k<<<grid, 256, 0, st>>>(p); break; }
+      case 2: { auto k = sweep_ell_warp_kernel<PT, AR, 2>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
+        k<<<grid, 256, 0, st>>>(p); break; }
+      case 4: { auto k = sweep_ell_warp_kernel<PT, AR, 4>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
+        k<<<grid, 256, 0, st>>>(p); break; }
+      case 8: { auto k = sweep_ell_warp_kernel<PT, AR, 8>;
+        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
+        k<<<grid, 256, 0, st>>>(p); break; }
       default: return MDP_EINVAL;
     }
   }
