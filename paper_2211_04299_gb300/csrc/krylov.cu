@@ -105,18 +105,19 @@ __device__ __forceinline__ MvIO<KT> resolve(const MatvecK& p) {
 }
 
 template <class KT>
-__device__ __forceinline__ void matvec_finish(const MatvecK& p, KT mx, KT ss) {
+__device__ __forceinline__ void matvec_finish(const MatvecK& p, KT mx, KT ss,
+                                              GridPos gp = this_grid()) {
   __shared__ KT shr[32];
   KT bm = block_max(mx, shr);
   KT bs = block_sum(ss, shr);
   KT* part = (KT*)p.partials;
   if (threadIdx.x == 0) {
-    part[2 * blockIdx.x] = bm;
-    part[2 * blockIdx.x + 1] = bs;
+    part[2 * gp.bid] = bm;
+    part[2 * gp.bid + 1] = bs;
   }
-  if (!arrive_last(p.counter)) return;
+  if (!arrive_last(p.counter, gp.nb)) return;
   KT m = 0, t = 0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = threadIdx.x; b < gp.nb; b += blockDim.x) {
     m = max(m, __ldcg(part + 2 * b));
     t += __ldcg(part + 2 * b + 1);
   }
@@ -162,7 +163,7 @@ __device__ __forceinline__ void matvec_finish(const MatvecK& p, KT mx, KT ss) {
 }
 
 template <class PT, class KT, int T>
-__global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
+__device__ __forceinline__ void matvec_ell_body(const MatvecK& p, GridPos gp) {
   const MvIO<KT> io = resolve<KT>(p);
   if (!io.run) return;
   const DevMDP& d = p.d;
@@ -174,8 +175,8 @@ __global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
   const KT ca = (KT)p.a, cb = (KT)p.b, cc = (KT)p.c;
   const uint64_t pol = l2_keep_policy();
   KT mx = 0, ss = 0;
-  const int64_t nteam_total = (int64_t)gridDim.x * nteams;
-  for (int64_t sb = (int64_t)blockIdx.x * nteams; sb < d.S; sb += nteam_total) {
+  const int64_t nteam_total = (int64_t)gp.nb * nteams;
+  for (int64_t sb = (int64_t)gp.bid * nteams; sb < d.S; sb += nteam_total) {
     const int64_t s = sb + team;
     const bool act = s < d.S;
     KT acc = 0;
@@ -211,7 +212,12 @@ __global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
       ss += r * r;
     }
   }
-  matvec_finish<KT>(p, mx, ss);
+  matvec_finish<KT>(p, mx, ss, gp);
+}
+
+template <class PT, class KT, int T>
+__global__ void __launch_bounds__(256) matvec_ell_kernel(MatvecK p) {
+  matvec_ell_body<PT, KT, T>(p, this_grid());
 }
 
 template <class PT, class KT>
@@ -537,16 +543,16 @@ template <> struct TSv<double> {
 
 // This block's range of vector units [u0, u1).
 template <class KT>
-__device__ __forceinline__ void block_units(int64_t S, int64_t& u0, int64_t& u1) {
+__device__ __forceinline__ void block_units(int64_t S, int64_t& u0, int64_t& u1, GridPos gp) {
   const int64_t nu = (S + TSv<KT>::R - 1) / TSv<KT>::R;
-  const int64_t per = (nu + gridDim.x - 1) / gridDim.x;
-  u0 = (int64_t)blockIdx.x * per;
+  const int64_t per = (nu + gp.nb - 1) / gp.nb;
+  u0 = (int64_t)gp.bid * per;
   u1 = min(nu, u0 + per);
 }
 
 // Sum acc[j] (j < m) over the block into part[blockIdx.x * (WMAX+1) + j].
 template <class KT, int MAXM>
-__device__ __forceinline__ void block_reduce_cols(KT (&acc)[MAXM], int m, KT* part) {
+__device__ __forceinline__ void block_reduce_cols(KT (&acc)[MAXM], int m, KT* part, GridPos gp) {
   __shared__ KT red[RED_THREADS / 32][MAXM];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -560,7 +566,7 @@ __device__ __forceinline__ void block_reduce_cols(KT (&acc)[MAXM], int m, KT* pa
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     KT x = 0;
     for (int w = 0; w < (int)(blockDim.x >> 5); ++w) x += red[w][j];
-    part[(int64_t)blockIdx.x * (WMAX + 1) + j] = x;
+    part[(int64_t)gp.bid * (WMAX + 1) + j] = x;
   }
 }
 
@@ -578,11 +584,12 @@ constexpr int TS_BATCH = 8;
 
 // Last block: out[j] = sum over blocks of part[b][j], j < m.
 template <class KT>
-__device__ __forceinline__ void reduce_dots(const KT* part, int m, double* outd, float* outf) {
+__device__ __forceinline__ void reduce_dots(const KT* part, int m, double* outd, float* outf,
+                                            GridPos gp) {
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int j = wid; j < m; j += nw) {
     KT acc = 0;
-    for (int b = lane; b < (int)gridDim.x; b += 32) acc += __ldcg(part + (int64_t)b * (WMAX + 1) + j);
+    for (int b = lane; b < gp.nb; b += 32) acc += __ldcg(part + (int64_t)b * (WMAX + 1) + j);
     acc = warp_sum(acc);
     if (lane == 0) {
       outd[j] = (double)acc;
@@ -595,7 +602,7 @@ __device__ __forceinline__ void reduce_dots(const KT* part, int m, double* outd,
 // fixed by the restart length, so the loop is static) and streams its vector units of w and
 // of every Q_j once.
 template <class KT, int MAXM>
-__global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
+__device__ __forceinline__ void cgs_dots_body(const KB& b, GridPos gp) {
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
@@ -603,7 +610,7 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
   const KT* w = (const KT*)((i & 1) ? b.w1 : b.w0);
   const KT* Q = (const KT*)b.Q;
   int64_t u0, u1;
-  block_units<KT>(b.S, u0, u1);
+  block_units<KT>(b.S, u0, u1, gp);
   KT acc[MAXM];
 #pragma unroll
   for (int j = 0; j < MAXM; ++j) acc[j] = 0;
@@ -621,15 +628,15 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
       }
     }
   }
-  block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials);
-  if (!arrive_last(b.counter)) return;
-  reduce_dots<KT>((const KT*)b.partials, m, c->c1, c->c1f);
+  block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials, gp);
+  if (!arrive_last(b.counter, gp.nb)) return;
+  reduce_dots<KT>((const KT*)b.partials, m, c->c1, c->c1f, gp);
 }
 
 // CGS2 pass 1 update and pass 2 projection: w -= Q c1, then c2 = Q^T w.  The second read of
 // each Q_j unit follows the first within the same thread and is served by L1.
 template <class KT, int MAXM>
-__global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
+__device__ __forceinline__ void cgs_axpy_dots_body(const KB& b, GridPos gp) {
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
@@ -639,7 +646,7 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
   __shared__ KT cf[WMAX + 1];
   stage_coefs<KT>(cf, c->c1, c->c1f, m);
   int64_t u0, u1;
-  block_units<KT>(b.S, u0, u1);
+  block_units<KT>(b.S, u0, u1, gp);
   KT acc[MAXM];
 #pragma unroll
   for (int j = 0; j < MAXM; ++j) acc[j] = 0;
@@ -669,9 +676,9 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
       }
     }
   }
-  block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials);
-  if (!arrive_last(b.counter)) return;
-  reduce_dots<KT>((const KT*)b.partials, m, c->c2, c->c2f);
+  block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials, gp);
+  if (!arrive_last(b.counter, gp.nb)) return;
+  reduce_dots<KT>((const KT*)b.partials, m, c->c2, c->c2f, gp);
 }
 
 // Givens update of column i of H and the stopping/restart decision (thread 0, FP64).
@@ -746,7 +753,7 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
 
 // CGS2 pass 2 update, ||w||_2 and the Givens step: w -= Q c2.
 template <class KT, int MAXM>
-__global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
+__device__ __forceinline__ void cgs_axpy_norm_body(const KB& b, GridPos gp) {
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
@@ -756,7 +763,7 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
   __shared__ KT cf[WMAX + 1];
   stage_coefs<KT>(cf, c->c2, c->c2f, m);
   int64_t u0, u1;
-  block_units<KT>(b.S, u0, u1);
+  block_units<KT>(b.S, u0, u1, gp);
   KT ss = 0;
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
     typename T::V wv = T::ld(w + u * T::R);
@@ -777,10 +784,10 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
   __shared__ KT shr[32];
   KT bs = block_sum(ss, shr);
   KT* part = (KT*)b.partials;
-  if (threadIdx.x == 0) part[blockIdx.x] = bs;
-  if (!arrive_last(b.counter)) return;
+  if (threadIdx.x == 0) part[gp.bid] = bs;
+  if (!arrive_last(b.counter, gp.nb)) return;
   KT t = 0;
-  for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) t += __ldcg(part + bb);
+  for (int bb = threadIdx.x; bb < gp.nb; bb += blockDim.x) t += __ldcg(part + bb);
   t = block_sum(t, shr);
   if (threadIdx.x == 0) givens_and_decide(c, sqrt((double)t), sizeof(KT) == 4);
 }
@@ -792,7 +799,7 @@ __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
 // decides: EST -> accept (or CHECK) when ||r||_inf meets the threshold, else the next step or
 // a restart; FINISH -> DONE with the candidate as the result.
 template <class KT, int MAXM>
-__global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
+__device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp) {
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   const int mode = *(volatile int*)&c->mode;
@@ -811,7 +818,7 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
   __syncthreads();
   const KT zl = est ? coef<KT>(c->z, c->zf, i + 1) * (KT)(1.0 / c->hnext) : KT(0);
   int64_t u0, u1;
-  block_units<KT>(b.S, u0, u1);
+  block_units<KT>(b.S, u0, u1, gp);
   KT mx = 0;
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
     typename T::V x = T::ld(base + u * T::R);
@@ -836,10 +843,10 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
   __shared__ KT shr[32];
   KT bm = block_max(mx, shr);
   KT* part = (KT*)b.partials;
-  if (threadIdx.x == 0) part[blockIdx.x] = bm;
-  if (!arrive_last(b.counter)) return;
+  if (threadIdx.x == 0) part[gp.bid] = bm;
+  if (!arrive_last(b.counter, gp.nb)) return;
   KT t = 0;
-  for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x) t = max(t, __ldcg(part + bb));
+  for (int bb = threadIdx.x; bb < gp.nb; bb += blockDim.x) t = max(t, __ldcg(part + bb));
   t = block_max(t, shr);
   if (threadIdx.x == 0) {
     if (mode == GM_FINISH) {
@@ -1034,6 +1041,23 @@ int launch_matvec(const MatvecLaunch& L, cudaStream_t st) {
   }
   if (L.d.pdt == MDP_F32) return launch_mv_typed<float, double>(L, st);
   return launch_mv_typed<double, double>(L, st);
+}
+
+template <class KT, int MAXM>
+__global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
+  cgs_dots_body<KT, MAXM>(b, this_grid());
+}
+template <class KT, int MAXM>
+__global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
+  cgs_axpy_dots_body<KT, MAXM>(b, this_grid());
+}
+template <class KT, int MAXM>
+__global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
+  cgs_axpy_norm_body<KT, MAXM>(b, this_grid());
+}
+template <class KT, int MAXM>
+__global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
+  estimate_candidate_body<KT, MAXM>(b, this_grid());
 }
 
 template <class KT, int MAXM>

@@ -193,19 +193,31 @@ template <typename T> __device__ __forceinline__ T block_max(T x, T* sh) {
 // partial results, then calls this; it returns true in exactly one block (the last to
 // arrive), which may then read all partials.  That block resets the counter to zero, so a
 // counter that starts at zero is zero again after every launch.
-__device__ __forceinline__ bool arrive_last(unsigned* counter) {
+// nb = number of blocks taking part (gridDim.x for a plain launch, the instance's block
+// count inside a batched launch).
+__device__ __forceinline__ bool arrive_last(unsigned* counter, int nb) {
   __shared__ bool am_last;
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
     unsigned t = atomicAdd(counter, 1u);
-    am_last = (t == gridDim.x - 1);
+    am_last = (t == (unsigned)nb - 1u);
     if (am_last) *counter = 0u;
   }
   __syncthreads();
   if (am_last) __threadfence();
   return am_last;
 }
+__device__ __forceinline__ bool arrive_last(unsigned* counter) { return arrive_last(counter, gridDim.x); }
+
+// Position of a block within the blocks that work on one instance: (blockIdx.x, gridDim.x)
+// for a plain launch; inside a batched launch, the block's index among its instance's
+// blocks and that instance's block count.
+struct GridPos {
+  int bid;
+  int nb;
+};
+__device__ __forceinline__ GridPos this_grid() { return GridPos{(int)blockIdx.x, (int)gridDim.x}; }
 
 // ------------------------------------------------------------------ bulk-copy pipeline
 // cp.async.bulk (TMA, untiled) global -> shared copies completing on an mbarrier, and the

@@ -229,7 +229,8 @@ __device__ __forceinline__ typename AR::MaxT load_maxt(const typename AR::MaxT* 
 // Block partials -> last block -> out (norms of Phi) and ref_out (norms of the reference
 // residual).  Partials: four arrays of MAX_RED_BLOCKS slots of 8 bytes.
 template <class AR>
-__device__ __forceinline__ void finish_norms(const SweepK& p, const Norms<AR>& nm) {
+__device__ __forceinline__ void finish_norms(const SweepK& p, const Norms<AR>& nm,
+                                             GridPos gp = this_grid()) {
   using R = typename AR::R;
   using M = typename AR::MaxT;
   __shared__ M shm[32];
@@ -243,15 +244,15 @@ __device__ __forceinline__ void finish_norms(const SweepK& p, const Norms<AR>& n
   R* ps = (R*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 16);
   R* ps2 = (R*)((char*)p.partials + (size_t)MAX_RED_BLOCKS * 24);
   if (threadIdx.x == 0) {
-    pm[blockIdx.x] = bm;
-    ps[blockIdx.x] = bs;
-    pm2[blockIdx.x] = bm2;
-    ps2[blockIdx.x] = bs2;
+    pm[gp.bid] = bm;
+    ps[gp.bid] = bs;
+    pm2[gp.bid] = bm2;
+    ps2[gp.bid] = bs2;
   }
-  if (!arrive_last(p.counter)) return;
+  if (!arrive_last(p.counter, gp.nb)) return;
   M m = AR::max0(), m2 = AR::max0();
   R t = 0, t2 = 0;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b = threadIdx.x; b < gp.nb; b += blockDim.x) {
     m = AR::mmax(m, load_maxt<AR>(pm, b));
     m2 = AR::mmax(m2, load_maxt<AR>(pm2, b));
     t += __ldcg(ps + b);
@@ -368,77 +369,6 @@ __global__ void __launch_bounds__(256) sweep_dense_kernel(SweepK p) {
       }
     }
     if (lane == 0) emit_state<AR>(p, s, pk, nm);
-  }
-  finish_norms<AR>(p, nm);
-}
-
-// ------------------------------------------------------------------ ELL: lane teams per row
-template <class PT, class AR, int T>
-__global__ void __launch_bounds__(256) sweep_ell_kernel(SweepK p) {
-  using V = typename AR::V;
-  using Qt = typename AR::Qt;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  Qt* Qsm = reinterpret_cast<Qt*>(smem_raw);
-  const DevMDP& d = p.d;
-  const int nteams = blockDim.x / T;
-  const int team = threadIdx.x / T, tl = threadIdx.x % T;
-  const int R = p.pi_in ? 1 : d.A;
-  const int SB = max(1, nteams / R);
-  const int64_t ntiles = (d.S + SB - 1) / SB;
-  const PT* val = (const PT*)d.P;
-  const int32_t* col = d.col;
-  const V* v = (const V*)p.v;
-  const int nvec = d.kp >> 2;
-  const uint64_t pol = l2_keep_policy();
-  Norms<AR> nm;
-  nm.init();
-  for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    const int64_t s0 = tile * SB;
-    const int ns = (int)((d.S - s0) < (int64_t)SB ? (d.S - s0) : (int64_t)SB);
-    const int nrows = ns * R;
-    for (int rb = 0; rb < nrows; rb += nteams) {
-      const int r = rb + team;
-      const bool act = r < nrows;
-      typename AR::Acc acc;
-      acc.init();
-      if (act) {
-        const int64_t s = s0 + r / R;
-        const int a = p.pi_in ? p.pi_in[s] : r % R;
-        const int64_t base = ((int64_t)s * d.A + a) * d.kp;
-        int it = 0;
-        for (int q = tl; q < nvec; q += T) {
-          Vec4<PT> pv;
-          pv.load(val + base + 4 * q);
-          int4 c4 = __ldcs(reinterpret_cast<const int4*>(col + base) + q);
-          acc.add(pv.e[0], ld_keep(v + c4.x, pol));
-          acc.add(pv.e[1], ld_keep(v + c4.y, pol));
-          acc.add(pv.e[2], ld_keep(v + c4.z, pol));
-          acc.add(pv.e[3], ld_keep(v + c4.w, pol));
-          if ((++it & 7) == 0) acc.fold();
-        }
-      }
-      Qt sum = AR::reduce_team(acc.result(), T);
-      if (act && tl == 0) {
-        const int64_t s = s0 + r / R;
-        const int a = p.pi_in ? p.pi_in[s] : r % R;
-        Qsm[r] = AR::qval(d, s, a, sum);
-      }
-    }
-    __syncthreads();
-    for (int st = threadIdx.x; st < ns; st += blockDim.x) {
-      const int64_t s = s0 + st;
-      Pick<AR> pk;
-      pk.init();
-      const int aref = p.pi_ref ? p.pi_ref[s] : -1;
-      if (p.pi_in) {
-        pk.consider(p.pi_in[s], Qsm[st], true, -1);
-      } else {
-        for (int a = 0; a < R; ++a)
-          pk.consider(a, Qsm[st * R + a], d.mask ? d.mask[s * d.A + a] != 0 : true, aref);
-      }
-      emit_state<AR>(p, s, pk, nm);
-    }
-    __syncthreads();
   }
   finish_norms<AR>(p, nm);
 }
@@ -754,13 +684,13 @@ __device__ __forceinline__ Cand<AR> cand_shfl(const Cand<AR>& x, int off) {
 }
 
 template <class PT, class AR, int T>
-__global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
+__device__ __forceinline__ void sweep_ell_body(const SweepK& p, GridPos gp) {
   using V = typename AR::V;
   using Qt = typename AR::Qt;
   const DevMDP& d = p.d;
   const int lane = threadIdx.x & 31;
-  const int64_t gw = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+  const int64_t gw = ((int64_t)gp.bid * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = (int64_t)gp.nb * (blockDim.x >> 5);
   const int R = p.pi_in ? 1 : d.A;
   constexpr int RPI = 32 / T;                  // row slots per pass
   int Rp = 1;
@@ -850,7 +780,12 @@ __global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
       emit_state<AR>(p, s, pk, nm);
     }
   }
-  finish_norms<AR>(p, nm);
+  finish_norms<AR>(p, nm, gp);
+}
+
+template <class PT, class AR, int T>
+__global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
+  sweep_ell_body<PT, AR, T>(p, this_grid());
 }
 
 template <class Kern>
