@@ -145,6 +145,14 @@ typedef struct {
  * order of floating-point additions.  Returns MDP_EINVAL for other values. */
 int mdp_set_tuning(mdp_t h, int32_t ell_lanes_sweep, int32_t ell_lanes_matvec);
 
+/* Block geometry of the ELL kernels: blocks of the Bellman sweep, of the P^pi matvec and of
+ * the Krylov vector kernels (0 = library choice, else 1..2048).  Norms and dot products are
+ * summed per block first, so the geometry fixes the order of floating-point additions; a
+ * batch reports each instance's geometry (mdp_batch_geometry) so that a single solve can
+ * reproduce that instance's results bit for bit.  ELL handles only, else MDP_EINVAL. */
+int mdp_set_geometry(mdp_t h, int32_t sweep_blocks, int32_t matvec_blocks,
+                     int32_t krylov_blocks);
+
 /* When on (nonzero), every Bellman-sweep and matvec launch is bracketed by CUDA events on
  * the handle's stream and its device time is added to mdp_stats.sweep_ms / matvec_ms. */
 int mdp_set_timing(mdp_t h, int on);
@@ -229,6 +237,46 @@ int opi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
               mdp_stats* stats);
 int opi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
                   mdp_stats* stats);
+
+/* ---------------------------------------------------------------------------- batches */
+/* A batch solves n independent MDPs with iGMRES-PI (Alg. 2, mixed precision) in one
+ * CUDA-graph launch: each instance runs the outer loop as a device-side state machine, and
+ * one loop iteration serves every instance with one launch per kernel family (Bellman sweep,
+ * P^pi matvec, CGS2, estimate, ...), each launch walking only the instances whose step is
+ * due.  Every instance's results equal those of ipi_solve on that handle alone with the
+ * batch's kernel shape (mdp_batch_geometry -> mdp_set_tuning + mdp_set_geometry).
+ *
+ * hs: n ELL handles with FP32 transition data on the current device; the batch reads their
+ * device data, so they must outlive it.  opts: shared options (NULL = defaults); precision
+ * must be MDP_PREC_MIXED, v0 NULL (every instance starts from V_0 = 0), 0 < alpha < 1.
+ * The batch allocates its workspace in one block at creation (mdp_batch_device_bytes).
+ * Errors: MDP_EINVAL (bad arguments), MDP_ENOMEM, MDP_EDEVICE. */
+typedef struct mdp_batch_s* mdp_batch_t;
+int mdp_batch_create(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_t* out);
+void mdp_batch_destroy(mdp_batch_t b);
+/* Stream for the batch's launches (a cudaStream_t; NULL = the batch's own stream). */
+int mdp_batch_set_stream(mdp_batch_t b, void* stream);
+/* Autotuner: for each ELL row length present, times the batched Bellman sweep and the
+ * batched matvec with 1, 2, 4 and 8 lanes per row and keeps the fastest (this changes only
+ * the order of floating-point additions).  Runs kernels on the batch's stream; synchronous. */
+int mdp_batch_tune(mdp_batch_t b);
+/* Kernel shape of instance i (any output may be NULL). */
+int mdp_batch_geometry(mdp_batch_t b, int32_t i, int32_t* lanes_sweep, int32_t* lanes_matvec,
+                       int32_t* sweep_blocks, int32_t* matvec_blocks, int32_t* krylov_blocks);
+int64_t mdp_batch_device_bytes(mdp_batch_t b);
+/* Solve every instance.  v_out[i]: S_i doubles = T(V_K); pi_out[i]: S_i ints = pi_K;
+ * stats[i] (stats may be NULL; launches counts the whole batch's kernels).  The pointer
+ * arrays are host arrays; the buffers they point to are host memory (mdp_batch_solve) or
+ * device memory (mdp_batch_solve_dev).  Synchronous.  Returns MDP_OK when every instance
+ * converged, MDP_ENOCONV when some reached max_outer (stats[i].status says which; their
+ * best v and pi are still written), MDP_ETIMEOUT when the loop guard ended the launch. */
+int mdp_batch_solve(mdp_batch_t b, double* const* v_out, int32_t* const* pi_out,
+                    mdp_stats* stats);
+int mdp_batch_solve_dev(mdp_batch_t b, double* const* v_out, int32_t* const* pi_out,
+                        mdp_stats* stats);
+/* One-shot form: create a batch of hs[0..n-1], solve into host buffers, destroy. */
+int ipi_solve_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, double* const* v_out,
+                    int32_t* const* pi_out, mdp_stats* stats);
 
 /* Message for the last nonzero return on this thread ("" if none). */
 const char* mdp_last_error(void);

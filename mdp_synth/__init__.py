@@ -85,9 +85,14 @@ def _distinct_columns(rng: np.random.Generator, lo: np.ndarray, width: int, k: i
     """For each row r draw k distinct integers uniformly from [lo[r], lo[r] + width).
 
     Sampling with replacement, then redrawing every row that holds a repeat, leaves each
-    accepted row uniform over the k-subsets (rejection sampling).
+    accepted row uniform over the k-subsets (rejection sampling).  When k > width / 4 the
+    acceptance rate collapses, so such rows take the first k entries of a uniformly random
+    permutation instead (also uniform over the k-subsets).
     """
     n = lo.shape[0]
+    if 4 * k > width:
+        # dense rows: rejection would rarely accept; take the first k of a random order
+        return np.argsort(rng.random((n, width)), axis=1)[:, :k].astype(np.int64) + lo[:, None]
     out = np.empty((n, k), dtype=np.int64)
     todo = np.arange(n)
     while todo.size:

@@ -18,6 +18,7 @@ from ._lib import (MDP_F32, MDP_F64, MDP_FLAG_HOST_LOOP, MDP_PREC_FP64,  # noqa:
 __all__ = [
     "MDPHandle", "mdp_create_dense", "mdp_create_ell", "bellman_apply", "policy_eval_gmres",
     "ipi_solve", "vi_solve", "pi_solve", "opi_solve", "opts", "MDP_PREC_FP64",
+    "MDPBatch", "ipi_solve_batch",
     "MDP_PREC_MIXED", "MDPError", "lib",
 ]
 
@@ -95,6 +96,11 @@ class MDPHandle:
 
     def set_tuning(self, ell_lanes_sweep: int = 0, ell_lanes_matvec: int = 0) -> None:
         _check(lib().mdp_set_tuning(self.ptr, ell_lanes_sweep, ell_lanes_matvec), "mdp_set_tuning")
+
+    def set_geometry(self, sweep_blocks: int = 0, matvec_blocks: int = 0,
+                     krylov_blocks: int = 0) -> None:
+        _check(lib().mdp_set_geometry(self.ptr, sweep_blocks, matvec_blocks, krylov_blocks),
+               "mdp_set_geometry")
 
 
 def mdp_create_dense(P, g, gamma: float, mask=None) -> MDPHandle:
@@ -233,3 +239,79 @@ def from_synth(m, device: bool = False) -> MDPHandle:
         return mdp_create_dense(np.ascontiguousarray(m.P), g, m.gamma, mask)
     return mdp_create_ell(np.ascontiguousarray(m.col, dtype=np.int32),
                           np.ascontiguousarray(m.val), g, m.gamma, mask)
+
+
+class MDPBatch:
+    """mdp_batch_t over ELL handles (mixed precision); keeps the handles alive."""
+
+    def __init__(self, handles, o=None):
+        self.handles = list(handles)
+        self.n = len(self.handles)
+        arr = (C.c_void_p * self.n)(*[h.ptr.value for h in self.handles])
+        self._p = C.c_void_p()
+        o = o or opts()
+        _check(lib().mdp_batch_create(arr, self.n, C.byref(o), C.byref(self._p)),
+               "mdp_batch_create")
+
+    @property
+    def ptr(self):
+        if self._p is None:
+            raise ValueError("batch is closed")
+        return self._p
+
+    def close(self):
+        if self._p is not None:
+            lib().mdp_batch_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream) -> None:
+        s = getattr(stream, "cuda_stream", stream)
+        _check(lib().mdp_batch_set_stream(self.ptr, C.c_void_p(s) if s else None),
+               "mdp_batch_set_stream")
+
+    def tune(self) -> None:
+        _check(lib().mdp_batch_tune(self.ptr), "mdp_batch_tune")
+
+    def geometry(self, i: int) -> dict:
+        v = [C.c_int32() for _ in range(5)]
+        _check(lib().mdp_batch_geometry(self.ptr, i, *[C.byref(x) for x in v]),
+               "mdp_batch_geometry")
+        keys = ("lanes_sweep", "lanes_matvec", "sweep_blocks", "matvec_blocks", "krylov_blocks")
+        return dict(zip(keys, (x.value for x in v)))
+
+    def device_bytes(self) -> int:
+        return int(lib().mdp_batch_device_bytes(self.ptr))
+
+    def solve(self, v_out=None, pi_out=None, device: bool = False):
+        """Solve every instance -> (list of v, list of pi, list of stats dicts, status)."""
+        if v_out is None:
+            v_out = [_new_like(h, device, "f64") for h in self.handles]
+        if pi_out is None:
+            pi_out = [_new_like(h, device, "i32") for h in self.handles]
+        dev = _is_cuda(v_out[0])
+        vp = (C.c_void_p * self.n)(*[_ptr(x).value for x in v_out])
+        pp = (C.c_void_p * self.n)(*[_ptr(x).value for x in pi_out])
+        st = (mdp_stats * self.n)()
+        fn = lib().mdp_batch_solve_dev if dev else lib().mdp_batch_solve
+        code = _check(fn(self.ptr, vp, pp, st), "mdp_batch_solve")
+        return v_out, pi_out, [s.as_dict() for s in st], code
+
+
+def ipi_solve_batch(handles, o=None):
+    """One-shot batched iGMRES-PI into host arrays -> (vs, pis, stats, status)."""
+    n = len(handles)
+    arr = (C.c_void_p * n)(*[h.ptr.value for h in handles])
+    vs = [np.empty(h.S, dtype=np.float64) for h in handles]
+    ps = [np.empty(h.S, dtype=np.int32) for h in handles]
+    vp = (C.c_void_p * n)(*[x.ctypes.data for x in vs])
+    pp = (C.c_void_p * n)(*[x.ctypes.data for x in ps])
+    st = (mdp_stats * n)()
+    o = o or opts()
+    code = _check(lib().ipi_solve_batch(arr, n, C.byref(o), vp, pp, st), "ipi_solve_batch")
+    return vs, ps, [s.as_dict() for s in st], code

@@ -58,6 +58,16 @@ SIGNATURES = {
     "mdp_opts_default": (mdp_opts, []),
     "mdp_set_timing": (C.c_int, [_h, C.c_int]),
     "mdp_set_tuning": (C.c_int, [_h, C.c_int32, C.c_int32]),
+    "mdp_set_geometry": (C.c_int, [_h, C.c_int32, C.c_int32, C.c_int32]),
+    "mdp_batch_create": (C.c_int, [C.POINTER(_h), C.c_int32, C.POINTER(mdp_opts), C.POINTER(_h)]),
+    "mdp_batch_destroy": (None, [_h]),
+    "mdp_batch_set_stream": (C.c_int, [_h, _vp]),
+    "mdp_batch_tune": (C.c_int, [_h]),
+    "mdp_batch_geometry": (C.c_int, [_h, C.c_int32, _ip, _ip, _ip, _ip, _ip]),
+    "mdp_batch_device_bytes": (C.c_int64, [_h]),
+    "mdp_batch_solve": (C.c_int, [_h, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(mdp_stats)]),
+    "mdp_batch_solve_dev": (C.c_int, [_h, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(mdp_stats)]),
+    "ipi_solve_batch": (C.c_int, [C.POINTER(_h), C.c_int32, C.POINTER(mdp_opts), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(mdp_stats)]),
     "bellman_apply": (C.c_int, [_h, _vp, _vp, _vp, _vp, C.c_int32]),
     "bellman_apply_dev": (C.c_int, [_h, _vp, _vp, _vp, _vp, _vp, C.c_int32]),
     "bellman_apply_ell_noalloc_dev": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp, _vp, _vp, _vp]),

@@ -85,6 +85,9 @@ struct mdp_s {
   int timing = 0;
   int lanes_sweep = 0;   // ELL lanes per row (0 = library choice)
   int lanes_matvec = 0;
+  int grid_sweep = 0;    // blocks per launch (0 = library choice)
+  int grid_matvec = 0;
+  int grid_krylov = 0;
   size_t data_bytes = 0;
   Workspace ws;
   // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
@@ -161,13 +164,8 @@ int ensure_ws(mdp_t h, int kt, int W) {
   return MDP_OK;
 }
 
-// Blocks of the tall-skinny Krylov kernels: about 256 rows per block, at most four per SM.
-int krylov_grid(mdp_t h) {
-  const int64_t S = h->d.S;
-  int64_t g = (S + 255) / 256;
-  g = std::min<int64_t>(g, (int64_t)num_sms() * 4);
-  return (int)std::max<int64_t>(1, std::min<int64_t>(g, MAX_RED_BLOCKS));
-}
+// Blocks of the tall-skinny Krylov kernels (mdp_set_geometry may fix them).
+int krylov_grid(mdp_t h) { return h->grid_krylov > 0 ? h->grid_krylov : krylov_blocks(h->d.S); }
 
 KrylovBufs kbufs(mdp_t h) {
   Workspace& w = h->ws;
@@ -266,6 +264,7 @@ int sweep(mdp_t h, int arith, const void* v, const int32_t* pi_in, int32_t* pi_o
   L.counter = h->ws.counter;
   L.err = h->ws.flags + 8;
   L.lanes = h->lanes_sweep;
+  L.grid = pi_in ? 0 : h->grid_sweep;
   int t = tic(h, pi_in ? 1 : 0);
   int r = launch_sweep(L, h->stream);
   toc(h, t);
@@ -330,7 +329,7 @@ int store_v(mdp_t h, const void* src, double* dst, int arith) {
   return MDP_OK;
 }
 
-int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st);
+int enqueue_step(mdp_t h, const int32_t* pi_dev, const void* rhs, cudaStream_t st);
 
 // One inner solve (Alg. 2 inner loop) on J^pi delta = rhs (rhs already in ws.phi, its norms
 // in ws.sout[slot]), with pi in ws.pi (or pi_dev).  thr: absolute target when alpha == 0.
@@ -351,7 +350,7 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   HostCtl hc{};
   RK(read_ctl(h, &hc));
   for (int it = 0; it <= max_steps + 1 && hc.mode != GM_DONE; ++it) {
-    RK(enqueue_step(h, pi_dev, h->stream));
+    RK(enqueue_step(h, pi_dev, rhs ? rhs : w.phi, h->stream));
     h->launches += 6;
     RK(read_ctl(h, &hc));
   }
@@ -373,8 +372,10 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
 }
 
 // The Arnoldi step as enqueued kernels (matvec, CGS2 + Givens, estimate + candidate, true
-// check); every kernel is gated on the device-resident mode.
-int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st) {
+// check); every kernel is gated on the device-resident mode.  rhs is the right-hand side of
+// the solve (Phi_k, or the exact residual when a solve resumes), used by the true-residual
+// matvec.
+int enqueue_step(mdp_t h, const int32_t* pi_dev, const void* rhs, cudaStream_t st) {
   Workspace& w = h->ws;
   KrylovBufs B = kbufs(h);
   MatvecLaunch M{};
@@ -398,6 +399,7 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st) {
   M.counter = w.counter;
   M.err = w.flags + 8;
   M.lanes = h->lanes_matvec;
+  M.grid = h->grid_matvec;
   MatvecLaunch C = M;
   C.gate_mode = GM_CHECK;
   C.gate_mode2 = GM_RESTART;
@@ -408,7 +410,7 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, cudaStream_t st) {
   C.a = -1.0;
   C.b = 1.0;
   C.c = h->d.gamma;
-  C.u = w.phi;
+  C.u = rhs;
   C.out = w.rbuf;
   C.qbase = nullptr;
   RK(launch_matvec(M, st));
@@ -485,7 +487,7 @@ int build_inner_graph(mdp_t h, int variant, const int32_t* pi_dev, double alpha,
   // loop body
   if (cudaStreamBeginCaptureToGraph(h->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return fail_graph(fail(MDP_EDEVICE, "body capture could not start"));
-  r = enqueue_step(h, pi_dev, h->cap);
+  r = enqueue_step(h, pi_dev, rhs, h->cap);
   if (r == MDP_OK) r = launch_loop_cond(hc, w.ctl, max_steps + 8, h->cap);
   if (r != MDP_OK) return fail_graph(r);
   cudaGraph_t b2 = nullptr;
@@ -802,6 +804,12 @@ int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int 
 }  // namespace
 
 // ====================================================================== C ABI
+namespace mdp {
+const DevMDP* handle_view(mdp_t h) { return h ? &h->d : nullptr; }
+int handle_device(mdp_t h) { return h ? h->device : -1; }
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace mdp
+
 extern "C" {
 
 mdp_opts mdp_opts_default(void) {
@@ -885,6 +893,23 @@ int mdp_set_tuning(mdp_t h, int32_t ell_lanes_sweep, int32_t ell_lanes_matvec) {
       cudaGraphExecDestroy(gg.exec);
       gg.exec = nullptr;
     }
+  return MDP_OK;
+}
+
+int mdp_set_geometry(mdp_t h, int32_t sweep_blocks, int32_t matvec_blocks, int32_t krylov_blocks) {
+  if (!h) return fail(MDP_EINVAL, "null handle");
+  if (h->d.kind != KIND_ELL) return fail(MDP_EINVAL, "block geometry applies to ELL handles");
+  const int32_t lim = MAX_RED_BLOCKS;
+  if (sweep_blocks < 0 || matvec_blocks < 0 || krylov_blocks < 0 || sweep_blocks > lim ||
+      matvec_blocks > lim || krylov_blocks > lim)
+    return fail(MDP_EINVAL, "block counts must be in 0..2048");
+  h->grid_sweep = sweep_blocks;
+  h->grid_matvec = matvec_blocks;
+  h->grid_krylov = krylov_blocks;
+  for (auto& gg : h->ig) {
+    if (gg.exec) cudaGraphExecDestroy(gg.exec);
+    gg.exec = nullptr;
+  }
   return MDP_OK;
 }
 

@@ -30,10 +30,7 @@ template <class KT> __device__ __forceinline__ KT scale_of(const GmresCtl* c);
 template <> __device__ __forceinline__ double scale_of<double>(const GmresCtl* c) { return c->xscale; }
 template <> __device__ __forceinline__ float scale_of<float>(const GmresCtl* c) { return c->xscalef; }
 
-__device__ __forceinline__ void set_scale(GmresCtl* c, double s) {
-  c->xscale = s;
-  c->xscalef = (float)s;
-}
+__device__ __forceinline__ void set_scale(GmresCtl* c, double s) { gmres_set_scale(c, s); }
 
 // Move to the next Arnoldi step of the cycle, or to a restart when the cycle is full.
 __device__ __forceinline__ void advance(GmresCtl* c) {
@@ -479,8 +476,7 @@ int launch_mv_typed(const MatvecLaunch& L, cudaStream_t st) {
     int grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, (d.S + 7) / 8);
     k<<<grid, 256, 0, st>>>(p);
   } else {
-    int T = L.lanes;
-    if (T <= 0) T = (d.kp / 4 >= 8) ? 8 : ((d.kp / 4 >= 4) ? 4 : ((d.kp / 4 >= 2) ? 2 : 1));
+    const int T = L.lanes > 0 ? L.lanes : ell_matvec_lanes_default(d);
     const int64_t units = (d.S + 256 / T - 1) / (256 / T);
     int grid = 1;
     switch (T) {
@@ -873,40 +869,7 @@ __device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp)
 
 __global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double sqrtS, int W,
                                   int max_steps, const SweepOut* rhs, int resume, int accept_est) {
-  c->W = W;
-  c->max_steps = max_steps;
-  c->sqrtS = sqrtS;
-  c->steps = 0;
-  c->restarts = 0;
-  c->est_runs = 0;
-  c->checks = 0;
-  c->loop_iters = 0;
-  c->i = 0;
-  c->dsel = 0;
-  c->from_rhs = 1;
-  c->status = GS_RUNNING;
-  c->last_inf = rhs->res_inf;
-  c->last_nrm2 = 0.0;
-  if (resume) {
-    c->thr = c->thr_saved;
-  } else {
-    c->thr = alpha > 0.0 ? alpha * rhs->res_inf : thr;
-    c->thr_saved = c->thr;
-  }
-  c->accept_est = accept_est;
-  c->resumed = resume;
-  const double beta = rhs->res_nrm2;
-  c->beta = beta;
-  for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
-  c->gv[0] = beta;
-  set_scale(c, beta > 0.0 ? 1.0 / beta : 0.0);
-  if (!(rhs->res_inf > c->thr) || beta == 0.0) {
-    // the start already meets the stopping rule: the result is delta_base = 0
-    c->mode = GM_DONE;
-    c->status = GS_CONVERGED;
-  } else {
-    c->mode = GM_STEP;
-  }
+  gmres_init_ctl(c, thr, alpha, sqrtS, W, max_steps, rhs, resume, accept_est);
 }
 
 __global__ void gmres_loop_cond_kernel(cudaGraphConditionalHandle hc, GmresCtl* c, int cap) {
@@ -1060,6 +1023,96 @@ __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
   estimate_candidate_body<KT, MAXM>(b, this_grid());
 }
 
+// ------------------------------------------------------------------ batched kernels
+// Launch parameters of one instance, staged in shared memory by thread 0 of the block.
+// which: 0 Arnoldi-step matvec, 1 true residual of the candidate (CHECK / RESTART),
+// 2 ungated timing run (out = rbuf - gamma P^pi rbuf into w0).
+__device__ __forceinline__ MatvecK batch_matvec_params(const BatchInst& I, int which) {
+  MatvecK p;
+  p.d = I.d;
+  p.pi = I.pib[I.cur];
+  p.x = nullptr;
+  p.ctl = I.ctl;
+  p.gate_mode = GM_STEP;
+  p.gate_mode2 = GM_STEP;
+  p.x_rhs = I.rbuf;
+  p.x_w0 = I.w0;
+  p.x_w1 = I.w1;
+  p.qbase = I.Q;
+  p.ldq = I.ldq;
+  p.a = 1.0;
+  p.b = 0.0;
+  p.c = -I.d.gamma;
+  p.u = nullptr;
+  p.out = nullptr;
+  p.out0 = I.w0;
+  p.out1 = I.w1;
+  p.norms = nullptr;
+  p.finalize_check = 0;
+  p.partials = I.partials;
+  p.counter = I.counter;
+  if (which == 1) {
+    p.gate_mode = GM_CHECK;
+    p.gate_mode2 = GM_RESTART;
+    p.x_w0 = I.d0;
+    p.x_w1 = I.d1;
+    p.qbase = nullptr;
+    p.a = -1.0;
+    p.b = 1.0;
+    p.c = I.d.gamma;
+    p.u = I.rhs_sel ? I.rref : I.phi;
+    p.out = I.rbuf;
+    p.finalize_check = 1;
+  } else if (which == 2) {
+    p.ctl = nullptr;
+    p.x = I.rbuf;
+    p.out = I.w0;
+  }
+  return p;
+}
+
+template <int T>
+__global__ void __launch_bounds__(256) batch_matvec_kernel(BatchDev B, int cls, int which) {
+  __shared__ MatvecK mp;
+  batch_for_each(B.mv[cls], [&](int j, GridPos gp) {
+    if (threadIdx.x == 0) mp = batch_matvec_params(B.insts[j], which);
+    __syncthreads();
+    matvec_ell_body<float, float, T>(mp, gp);
+  });
+}
+
+__device__ __forceinline__ KB batch_kb(const BatchInst& I) {
+  return KB{I.d.S, I.ldq, I.Q, I.w0, I.w1, I.rbuf, I.d0, I.d1, I.partials, I.counter, I.ctl};
+}
+
+template <int MAXM, int STAGE>
+__global__ void __launch_bounds__(RED_THREADS) batch_ts_kernel(BatchDev B) {
+  __shared__ KB kb;
+  batch_for_each(B.ts, [&](int j, GridPos gp) {
+    if (threadIdx.x == 0) kb = batch_kb(B.insts[j]);
+    __syncthreads();
+    if (STAGE == 0) cgs_dots_body<float, MAXM>(kb, gp);
+    else if (STAGE == 1) cgs_axpy_dots_body<float, MAXM>(kb, gp);
+    else if (STAGE == 2) cgs_axpy_norm_body<float, MAXM>(kb, gp);
+    else estimate_candidate_body<float, MAXM>(kb, gp);
+  });
+}
+
+template <int MAXM>
+void launch_batch_ts(const BatchDev& B, int first_stage, int last_stage, int grid, cudaStream_t st) {
+  if (first_stage <= 0 && 0 <= last_stage) batch_ts_kernel<MAXM, 0><<<grid, RED_THREADS, 0, st>>>(B);
+  if (first_stage <= 1 && 1 <= last_stage) batch_ts_kernel<MAXM, 1><<<grid, RED_THREADS, 0, st>>>(B);
+  if (first_stage <= 2 && 2 <= last_stage) batch_ts_kernel<MAXM, 2><<<grid, RED_THREADS, 0, st>>>(B);
+  if (first_stage <= 3 && 3 <= last_stage) batch_ts_kernel<MAXM, 3><<<grid, RED_THREADS, 0, st>>>(B);
+}
+
+void launch_batch_ts_m(const BatchDev& B, int maxm, int s0, int s1, int grid, cudaStream_t st) {
+  if (maxm <= 8) launch_batch_ts<8>(B, s0, s1, grid, st);
+  else if (maxm <= 16) launch_batch_ts<16>(B, s0, s1, grid, st);
+  else if (maxm <= 32) launch_batch_ts<32>(B, s0, s1, grid, st);
+  else launch_batch_ts<64>(B, s0, s1, grid, st);
+}
+
 template <class KT, int MAXM>
 void launch_cgs_typed(const KB& b, int grid, cudaStream_t st) {
   cgs_dots_kernel<KT, MAXM><<<grid, RED_THREADS, 0, st>>>(b);
@@ -1092,6 +1145,64 @@ int launch_estimate(const KrylovBufs& B, cudaStream_t st) {
   KB b = make_kb(B);
   if (B.kt == 1) launch_est_kt<float>(b, B.grid, B.maxm, st);
   else launch_est_kt<double>(b, B.grid, B.maxm, st);
+  return ok_or_dev();
+}
+
+int ell_matvec_lanes_default(const DevMDP& d) {
+  const int nvec = d.kp / 4;
+  return nvec >= 8 ? 8 : (nvec >= 4 ? 4 : (nvec >= 2 ? 2 : 1));
+}
+
+// Blocks of the single-instance tall-skinny Krylov kernels: about 256 rows per block, at
+// most four blocks per SM.
+int krylov_blocks(int64_t S) {
+  int64_t g = (S + 255) / 256;
+  g = std::min<int64_t>(g, (int64_t)num_sms() * 4);
+  return (int)std::max<int64_t>(1, std::min<int64_t>(g, MAX_RED_BLOCKS));
+}
+
+int batch_matvec_grid(int cls) {
+  int per_sm = 1;
+  cudaError_t e = cudaSuccess;
+  switch (cls) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<1>, 256, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<2>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<4>, 256, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<8>, 256, 0); break;
+  }
+  if (e != cudaSuccess) { cudaGetLastError(); per_sm = 1; }
+  return num_sms() * std::max(per_sm, 1);
+}
+
+int launch_batch_matvec(const BatchDev& B, int cls, int which, int grid, cudaStream_t st) {
+  switch (cls) {
+    case 0: batch_matvec_kernel<1><<<grid, 256, 0, st>>>(B, cls, which); break;
+    case 1: batch_matvec_kernel<2><<<grid, 256, 0, st>>>(B, cls, which); break;
+    case 2: batch_matvec_kernel<4><<<grid, 256, 0, st>>>(B, cls, which); break;
+    case 3: batch_matvec_kernel<8><<<grid, 256, 0, st>>>(B, cls, which); break;
+    default: return MDP_EINVAL;
+  }
+  return ok_or_dev();
+}
+
+int batch_ts_grid(int maxm) {
+  int per_sm = 1;
+  cudaError_t e;
+  if (maxm <= 8) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ts_kernel<8, 1>, RED_THREADS, 0);
+  else if (maxm <= 16) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ts_kernel<16, 1>, RED_THREADS, 0);
+  else if (maxm <= 32) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ts_kernel<32, 1>, RED_THREADS, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_ts_kernel<64, 1>, RED_THREADS, 0);
+  if (e != cudaSuccess) { cudaGetLastError(); per_sm = 1; }
+  return num_sms() * std::max(per_sm, 1);
+}
+
+int launch_batch_cgs(const BatchDev& B, int maxm, int grid, cudaStream_t st) {
+  launch_batch_ts_m(B, maxm, 0, 2, grid, st);
+  return ok_or_dev();
+}
+
+int launch_batch_estimate(const BatchDev& B, int maxm, int grid, cudaStream_t st) {
+  launch_batch_ts_m(B, maxm, 3, 3, grid, st);
   return ok_or_dev();
 }
 

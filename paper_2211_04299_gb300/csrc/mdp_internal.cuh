@@ -287,6 +287,12 @@ enum GmresMode {
 
 enum GmresStatus { GS_RUNNING = 0, GS_CONVERGED = 1, GS_BREAKDOWN = 2, GS_CAP = 3 };
 
+// Scalars produced by the Bellman sweep and by reduction kernels.
+struct SweepOut {
+  double res_inf;   // ||Phi||_inf
+  double res_nrm2;  // ||Phi||_2
+};
+
 struct GmresCtl {
   int mode;
   int status;
@@ -319,11 +325,52 @@ struct GmresCtl {
   float xscalef;
 };
 
-// Scalars produced by the Bellman sweep and by reduction kernels.
-struct SweepOut {
-  double res_inf;   // ||Phi||_inf
-  double res_nrm2;  // ||Phi||_2
-};
+__device__ __forceinline__ void gmres_set_scale(GmresCtl* c, double s) {
+  c->xscale = s;
+  c->xscalef = (float)s;
+}
+
+// Start an inner solve of J^pi delta = r (Krylov init, Sec. 2.2): beta = ||r||_2 from the
+// norms of r, threshold alpha ||r||_inf (or thr when alpha == 0; the saved threshold when
+// resuming), first basis vector r / beta.  A start that already meets the threshold ends at
+// once with delta = 0.
+__device__ inline void gmres_init_ctl(GmresCtl* c, double thr, double alpha, double sqrtS, int W,
+                                      int max_steps, const SweepOut* rhs, int resume,
+                                      int accept_est) {
+  c->W = W;
+  c->max_steps = max_steps;
+  c->sqrtS = sqrtS;
+  c->steps = 0;
+  c->restarts = 0;
+  c->est_runs = 0;
+  c->checks = 0;
+  c->loop_iters = 0;
+  c->i = 0;
+  c->dsel = 0;
+  c->from_rhs = 1;
+  c->status = GS_RUNNING;
+  c->last_inf = rhs->res_inf;
+  c->last_nrm2 = 0.0;
+  if (resume) {
+    c->thr = c->thr_saved;
+  } else {
+    c->thr = alpha > 0.0 ? alpha * rhs->res_inf : thr;
+    c->thr_saved = c->thr;
+  }
+  c->accept_est = accept_est;
+  c->resumed = resume;
+  const double beta = rhs->res_nrm2;
+  c->beta = beta;
+  for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
+  c->gv[0] = beta;
+  gmres_set_scale(c, beta > 0.0 ? 1.0 / beta : 0.0);
+  if (!(rhs->res_inf > c->thr) || beta == 0.0) {
+    c->mode = GM_DONE;
+    c->status = GS_CONVERGED;
+  } else {
+    c->mode = GM_STEP;
+  }
+}
 
 // ------------------------------------------------------------------ launch descriptors
 struct SweepLaunch {
@@ -428,6 +475,112 @@ int launch_validate(const DevMDP& d, int* flags, cudaStream_t st);
 // flags[5] |= 1 when a policy entry is out of range or disallowed by the mask.
 int launch_check_policy(const int32_t* pi, int64_t S, int32_t A, const uint8_t* mask, int* flags,
                         cudaStream_t st);
+
+// ------------------------------------------------------------------ batched iGMRES-PI
+// A batch solves many independent ELL MDPs (FP32 P, mixed precision) with one graph launch.
+// Each instance runs Alg. 2 as a device-side state machine:
+//   SWEEP0 (first Bellman sweep) -> INNER (Arnoldi steps; GmresCtl.mode) -> SWEEPV (the
+//   sweep that gives pi_{k+1}, Phi_{k+1} and the exact inner residual of pi_k) -> INNER ... -> DONE
+// One loop iteration runs every kernel once over the instances that are in the matching
+// phase.  An instance is cut into "virtual blocks" per kernel family; a batched kernel walks
+// the virtual blocks of a compacted list of instances with a grid-stride loop, and each
+// virtual block runs the same kernel body as a single-instance launch whose grid has that
+// instance's block count, so results do not depend on the batch.
+enum BatchPhase { BP_SWEEP0 = 0, BP_INNER = 1, BP_SWEEPV = 2, BP_DONE = 3 };
+constexpr int BATCH_CLASSES = 4;  // ELL lanes per row 1, 2, 4, 8 (class = log2)
+
+struct BatchInst {
+  DevMDP d;
+  int64_t ldq;
+  float2* v;        // V_k (double-float)
+  float2* tv;       // T V_k
+  float* phi;       // Phi_k = T V_k - V_k
+  float* rref;      // exact residual of pi_k at V_{k+1}
+  float* Q;         // Krylov basis [W+1][ldq]
+  float* w0;
+  float* w1;
+  float* rbuf;
+  float* d0;
+  float* d1;
+  int32_t* pib[2];  // policy double buffer: pi_k = pib[cur]
+  GmresCtl* ctl;
+  SweepOut* sout;   // [4]
+  void* partials;
+  unsigned* counter;
+  double sqrtS;
+  int nb_sw, nb_mv, nb_ts, nb_ew;  // virtual blocks per kernel family
+  int cls_sw, cls_mv;              // ELL lane class of the sweep / matvec
+  // state
+  int phase, cur, k, reps, status, starting, rhs_sel;
+  int inner, restarts, checks, sweeps, loops;
+  double thr, res;
+};
+
+struct BatchList {  // active instances of one kernel family, with block prefix sums
+  int* inst;        // [n]
+  int* first;       // [n + 1]; the blocks of inst[j] are first[j] .. first[j+1]-1
+  int* count;       // number of listed instances
+};
+
+struct BatchDev {
+  BatchInst* insts;
+  int n;
+  double alpha, tol;
+  int W, max_steps, max_outer;
+  BatchList sw[BATCH_CLASSES];  // sweeps due (by sweep lane class)
+  BatchList mv[BATCH_CLASSES];  // inner solves running (by matvec lane class)
+  BatchList ts;                 // inner solves running (tall-skinny kernels)
+  BatchList ew;                 // inner solves running (element-wise kernels)
+  BatchList all;                // every instance (element-wise kernels)
+  double** vout;                // [n] output T(V_K) per instance
+  int32_t** pout;               // [n] output pi_K per instance
+  int* ctr;                     // [0] instances not done, [1] loop iterations, [2] guard hit
+  int max_iters;
+};
+
+// Position of a block among the virtual blocks of one instance (binary search in first[]).
+__device__ __forceinline__ int batch_slot(const int* first, int cnt, int vb) {
+  int lo = 0, hi = cnt - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (first[mid] <= vb) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Run f(instance, GridPos) for every virtual block of list L (grid-stride over blocks).
+template <class F>
+__device__ __forceinline__ void batch_for_each(const BatchList& L, F&& f) {
+  const int cnt = *(volatile const int*)L.count;
+  if (cnt <= 0) return;
+  const int total = L.first[cnt];
+  for (int vb = blockIdx.x; vb < total; vb += gridDim.x) {
+    const int j = batch_slot(L.first, cnt, vb);
+    const int f0 = L.first[j];
+    f(L.inst[j], GridPos{vb - f0, L.first[j + 1] - f0});
+    __syncthreads();
+  }
+}
+
+// Batched kernel families (sweep.cu, krylov.cu).  grid = physical blocks.
+int launch_batch_sweep(const BatchDev& B, int cls, int grid, cudaStream_t st);
+int batch_sweep_grid(int cls);
+// which: 0 Arnoldi-step matvec, 1 true-residual matvec (CHECK / RESTART), 2 timing only
+int launch_batch_matvec(const BatchDev& B, int cls, int which, int grid, cudaStream_t st);
+int batch_matvec_grid(int cls);
+int launch_batch_cgs(const BatchDev& B, int maxm, int grid, cudaStream_t st);
+int launch_batch_estimate(const BatchDev& B, int maxm, int grid, cudaStream_t st);
+int batch_ts_grid(int maxm);
+// Block counts of the single-instance ELL kernels (library choice), shared with the batch.
+int ell_sweep_lanes_default(const DevMDP& d);
+int ell_matvec_lanes_default(const DevMDP& d);
+int krylov_blocks(int64_t S);
+
+// Handle access for the batch driver (api.cu): the device view of a handle's data, its
+// device, and the thread-local error message of mdp_last_error.
+const DevMDP* handle_view(mdp_t h);
+int handle_device(mdp_t h);
+int set_error(int code, const char* msg);
 
 int num_sms();
 

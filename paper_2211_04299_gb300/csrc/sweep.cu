@@ -788,6 +788,39 @@ __global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
   sweep_ell_body<PT, AR, T>(p, this_grid());
 }
 
+// Batched sweep: the virtual blocks of every instance whose sweep is due (class cls).  The
+// launch parameters of an instance are staged in shared memory by thread 0.  Phase SWEEP0
+// writes pi_k; phase SWEEPV writes the candidate pi_{k+1} into the other policy buffer and
+// the exact residual of pi_k (the reference policy) into rref.
+template <int T>
+__global__ void __launch_bounds__(256, 3) batch_sweep_kernel(BatchDev B, int cls) {
+  __shared__ SweepK sp;
+  batch_for_each(B.sw[cls], [&](int j, GridPos gp) {
+    if (threadIdx.x == 0) {
+      const BatchInst& I = B.insts[j];
+      const bool verify = I.phase == BP_SWEEPV;
+      SweepK p;
+      p.d = I.d;
+      p.v = I.v;
+      p.pi_in = nullptr;
+      p.pi_out = I.pib[verify ? 1 - I.cur : I.cur];
+      p.tv_out = I.tv;
+      p.tv64_out = nullptr;
+      p.phi_out = I.phi;
+      p.margin_out = nullptr;
+      p.pi_ref = verify ? I.pib[I.cur] : nullptr;
+      p.rref_out = verify ? (void*)I.rref : nullptr;
+      p.out = I.sout;
+      p.ref_out = verify ? I.sout + 2 : nullptr;
+      p.partials = I.partials;
+      p.counter = I.counter;
+      sp = p;
+    }
+    __syncthreads();
+    sweep_ell_body<float, ArDF, T>(sp, gp);
+  });
+}
+
 template <class Kern>
 int grid_for(Kern k, int threads, size_t smem, int64_t work_units) {
   int per_sm = 0;
@@ -838,11 +871,7 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
     int grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, (d.S + 7) / 8);
     k<<<grid, 256, 0, st>>>(p);
   } else {
-    int T = L.lanes;
-    if (T <= 0) {
-      const int nvec = d.kp / 4;
-      T = nvec >= 8 ? 2 : 1;
-    }
+    const int T = L.lanes > 0 ? L.lanes : ell_sweep_lanes_default(d);
     const int64_t units = (d.S + 7) / 8;
     int grid = 1;
     switch (T) {
@@ -865,6 +894,32 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
 }
 
 }  // namespace
+
+int ell_sweep_lanes_default(const DevMDP& d) { return (d.kp / 4) >= 8 ? 2 : 1; }
+
+int batch_sweep_grid(int cls) {
+  int per_sm = 1;
+  cudaError_t e = cudaSuccess;
+  switch (cls) {
+    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<1>, 256, 0); break;
+    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<2>, 256, 0); break;
+    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<4>, 256, 0); break;
+    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<8>, 256, 0); break;
+  }
+  if (e != cudaSuccess) { cudaGetLastError(); per_sm = 1; }
+  return num_sms() * std::max(per_sm, 1);
+}
+
+int launch_batch_sweep(const BatchDev& B, int cls, int grid, cudaStream_t st) {
+  switch (cls) {
+    case 0: batch_sweep_kernel<1><<<grid, 256, 0, st>>>(B, cls); break;
+    case 1: batch_sweep_kernel<2><<<grid, 256, 0, st>>>(B, cls); break;
+    case 2: batch_sweep_kernel<4><<<grid, 256, 0, st>>>(B, cls); break;
+    case 3: batch_sweep_kernel<8><<<grid, 256, 0, st>>>(B, cls); break;
+    default: return MDP_EINVAL;
+  }
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
 
 int launch_sweep(const SweepLaunch& L, cudaStream_t st) {
   if (L.arith == 1) {

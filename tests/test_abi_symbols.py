@@ -55,6 +55,28 @@ def test_invalid_arguments_fail_before_any_device_work(built):
     assert lib.mdp_create_ell(4, 1, 9, None, None, 0, None, 0.9, None, ctypes.byref(h)) == _lib.MDP_EINVAL
     assert lib.mdp_create_ell(4, 1, 2, None, None, 0, None, 1.5, None, ctypes.byref(h)) == _lib.MDP_EINVAL
     assert lib.ipi_solve(None, None, None, None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_set_geometry(None, 0, 0, 0) == _lib.MDP_EINVAL
+    # batches: argument and option checks precede any device work
+    b = ctypes.c_void_p()
+    assert lib.mdp_batch_create(None, 0, None, ctypes.byref(b)) == _lib.MDP_EINVAL
+    one = (ctypes.c_void_p * 1)(None)
+    assert lib.mdp_batch_create(one, 1, None, None) == _lib.MDP_EINVAL
+    o = lib.mdp_opts_default()
+    o.precision = _lib.MDP_PREC_FP64
+    assert lib.mdp_batch_create(one, 1, ctypes.byref(o), ctypes.byref(b)) == _lib.MDP_EINVAL
+    assert b"MIXED" in lib.mdp_last_error()
+    o = lib.mdp_opts_default()
+    o.restart = 0
+    assert lib.mdp_batch_create(one, 1, ctypes.byref(o), ctypes.byref(b)) == _lib.MDP_EINVAL
+    assert not b.value
+    assert lib.mdp_batch_solve(None, None, None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_batch_solve_dev(None, None, None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_batch_geometry(None, 0, None, None, None, None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_batch_tune(None) == _lib.MDP_EINVAL
+    assert lib.mdp_batch_set_stream(None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_batch_device_bytes(None) == 0
+    assert lib.ipi_solve_batch(None, 0, None, None, None, None) == _lib.MDP_EINVAL
+    lib.mdp_batch_destroy(None)
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):
