@@ -51,9 +51,14 @@ def parse():
     ap.add_argument("--S", type=int, default=S_,
                     help="states of the dense (or, with --config 3, banded) workload; other "
                          "values only for profiling")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
                     help="workload: 2 = the paper-scale dense MDP (the benchmark), 1 = small "
-                         "ELL, 3 = S=10^6 banded ELL (for measurement of the ELL kernels)")
+                         "ELL, 3 = S=10^6 banded ELL (for measurement of the ELL kernels), "
+                         "4 = a batch of 256 independent ELL MDPs solved together")
+    ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="batched workload: keep the library's lanes per row (no autotuning), "
+                         "so the launch sequence is the same on every run (for profilers)")
     return ap.parse_args()
 
 
@@ -200,10 +205,48 @@ def cores_used():
         return os.cpu_count() or 1
 
 
+def reference_arm_batch(args):
+    """The oracle on the batched workload: each step solves the next instance of the batch
+    (Alg. 2 to 1e-8); the rate is instances per second of oracle time."""
+    import mdp_synth
+    import oracle
+    specs = mdp_synth.batch_specs(args.batch, mdp_synth.CONFIG_SEEDS[4])
+    total, wall = 0.0, 0.0
+    j = 0
+    for i in range(args.warmup + args.steps):
+        syn = mdp_synth.instance_from_spec(specs[j % len(specs)])
+        j += 1
+        m = oracle.from_synth(syn)
+        t0 = time.perf_counter()
+        oracle.gmres_policy_iteration(m, alpha=ALPHA, W=W_, tol=TOL)
+        dt = time.perf_counter() - t0
+        if i >= args.warmup:
+            total += dt
+    value = args.steps / total
+    cores = cores_used()
+    sample = (f"per step: one oracle iGMRES-PI solve of the next instance of the batch "
+              f"(instances {args.warmup}..{args.warmup + args.steps - 1} of {args.batch})")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(n=args.batch)},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
+    if args.config == 4:
+        return reference_arm_batch(args)
     import mdp_synth
     import oracle
     counts = oracle_counts()
@@ -237,6 +280,207 @@ def reference_arm(args):
     return 0
 
 
+# ---------------------------------------------------------------- batched workload
+BATCH_WORKLOAD = ("batch of {n} independent ELL MDPs: S log-uniform in [500, 50000], A uniform "
+                  "in 2..16, k in {{8, 16, 32}}, gamma in {{0.9, 0.99, 0.999}}, FP32 values, "
+                  "g~U(0,1); iGMRES-PI mixed FP32/double-float, alpha=0.1, W=30, tol 1e-8, all "
+                  "instances in one CUDA-graph launch")
+
+
+def oracle_batch_sample(syns, budget_s=12.0):
+    """Oracle iGMRES-PI (Alg. 2) solves of the batch's first instances (an i.i.d. sample of
+    its distribution) until about budget_s seconds of CPU time -> (solves/s, instances, s)."""
+    import oracle
+    t_tot, n = 0.0, 0
+    for syn in syns:
+        m = oracle.from_synth(syn)
+        t0 = time.perf_counter()
+        oracle.gmres_policy_iteration(m, alpha=ALPHA, W=W_, tol=TOL)
+        t_tot += time.perf_counter() - t0
+        n += 1
+        if t_tot >= budget_s:
+            break
+    return n / t_tot, n, t_tot
+
+
+def run_batch_bench(args, mg, torch, dist, world, rank, local):
+    import mdp_synth
+    n = args.batch
+    specs = mdp_synth.batch_specs(n, mdp_synth.CONFIG_SEEDS[4])
+    syns = [mdp_synth.instance_from_spec(sp) for sp in specs]
+    hs = [mg.from_synth(syn) for syn in syns]
+    # a stream of our own: the CUDA events below must be recorded on the stream the batch
+    # launches on (torch's default stream is the legacy stream, handle 0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
+                flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0)
+    b = mg.MDPBatch(hs, o)
+    b.set_stream(stream)
+    if not args.no_tune:
+        b.tune()
+    vd = [torch.empty(h.S, dtype=torch.float64, device="cuda") for h in hs]
+    pd = [torch.empty(h.S, dtype=torch.int32, device="cuda") for h in hs]
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    warm = max(3, args.warmup)
+    for _ in range(warm):
+        b.solve(vd, pd)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    stats = []
+    ev[0].record(stream)
+    for i in range(args.steps):
+        _, _, st, code = b.solve(vd, pd)
+        ev[i + 1].record(stream)
+        stats.append((st, code))
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    elapsed_ms = ev[0].elapsed_time(ev[-1])
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t.item())
+    value = world * n * args.steps / (elapsed_ms / 1000.0)
+    ok = all(code == 0 and all(x["status"] == 0 and x["residual_inf"] <= TOL for x in st)
+             for st, code in stats)
+    st_last = stats[-1][0]
+
+    # dominant kernel family: the batched Bellman sweep over every instance, timed alone
+    peak, peak_kind = peaks()
+    sb = float(sum(sweep_algorithmic_bytes(syn) for syn in syns))
+    reps = 20
+    b.bellman(wait=False)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        b.bellman(wait=False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sweep_ms = e0.elapsed_time(e1) / reps
+    sweep_gbs = sb / (sweep_ms * 1e-3) / 1e9
+    launches = int(sum(st[0]["launches"] for st, _ in stats))
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": args.steps, "warmup": warm, "ms_per_step": elapsed_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: f32 P/Krylov, double-float (2xf32) values, f64 Givens",
+        "data": "synthetic",
+        "config": {"workload": BATCH_WORKLOAD.format(n=n), "instances": n,
+                   "states_total": int(sum(syn.S for syn in syns)),
+                   "nonzeros_total": int(sum(syn.S * syn.A * syn.k for syn in syns)),
+                   "tol": TOL, "alpha": ALPHA, "restart": W_, "precision": "mixed",
+                   "parallelism": f"replicas x{world}",
+                   "l2": f"inputs larger than L2 ({sb / 1e9:.2f} GB per batched sweep); no flush"},
+        "step": "one batched solve of every instance (solves/s counts instances)",
+        "converged": ok,
+        "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                       "p99": float(np.percentile(step_ms, 99)),
+                       "note": "every instance of a batch completes when the batch does"},
+        "per_batch": {"loop_iterations_launches": st_last[0]["launches"],
+                      "outer_max": max(x["outer"] for x in st_last),
+                      "inner_sum": int(sum(x["inner"] for x in st_last)),
+                      "sweeps_sum": int(sum(x["sweeps"] for x in st_last))},
+        "bellman_sweep": {"ms": sweep_ms, "gbs": sweep_gbs, "algorithmic_bytes": sb,
+                          "scope": "one batched sweep of all instances"},
+        "roofline": {"bound": "hbm", "kernel": "batch_sweep_kernel", "achieved": sweep_gbs,
+                     "peak": peak, "unit": "GB/s", "frac": sweep_gbs / peak,
+                     "peak_source": peak_kind, "traffic": None},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+
+    if not args.no_e2e:
+        # through the host-pointer API: upload every instance's P and g from pinned memory,
+        # solve the batch, copy every v and pi back
+        pins = [(torch.from_numpy(np.ascontiguousarray(syn.col)).pin_memory(),
+                 torch.from_numpy(np.ascontiguousarray(syn.val)).pin_memory(),
+                 np.ascontiguousarray(syn.g)) for syn in syns]
+        in_bytes = int(sum(c.numel() * 4 + v.numel() * 4 + g.nbytes for c, v, g in pins))
+        vh = [np.empty(syn.S) for syn in syns]
+        ph = [np.empty(syn.S, np.int32) for syn in syns]
+        out_bytes = int(sum(x.nbytes for x in vh) + sum(x.nbytes for x in ph))
+
+        def e2e_step():
+            for h, (c, v, g) in zip(hs, pins):
+                mg.mdp_load_ell(h, c.numpy(), v.numpy(), g)
+            b.solve(vh, ph)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e2e_steps = min(args.steps, 3)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        line["e2e"] = {"value": world * n * e2e_steps / float(tt.item()), "unit": "solves/s",
+                       "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
+                       "steps": e2e_steps}
+        del pins
+
+    if not args.no_fp64:
+        # the plain per-instance forms on the same MDPs: FP64 (P widened exactly) and the
+        # single-instance mixed solver, one solve after another
+        def per_instance(make_handle, prec):
+            tot = 0.0
+            for syn, h0 in zip(syns, hs):
+                h = make_handle(syn, h0)
+                h.set_stream(stream)
+                oo = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision=prec)
+                vo = torch.empty(syn.S, dtype=torch.float64, device="cuda")
+                po = torch.empty(syn.S, dtype=torch.int32, device="cuda")
+                mg.ipi_solve(h, oo, v_out=vo, pi_out=po)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                mg.ipi_solve(h, oo, v_out=vo, pi_out=po)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                tot += a0.elapsed_time(a1)
+                if h is not h0:
+                    h.close()
+            return n / (tot / 1000.0), tot
+
+        def fp64_handle(syn, h0):
+            return mg.from_synth(mdp_synth.SynthMDP(S=syn.S, A=syn.A, gamma=syn.gamma, g=syn.g,
+                                                    kind="ell", col=syn.col,
+                                                    val=syn.val.astype(np.float64)), device=False)
+
+        v64, ms64 = per_instance(fp64_handle, "fp64")
+        vmx, msmx = per_instance(lambda syn, h0: h0, "mixed")
+        line["fp64_plain"] = {"value": v64, "unit": "solves/s", "ms_total": ms64,
+                              "form": "one ipi_solve per instance, FP64 P and Krylov"}
+        line["mixed_single"] = {"value": vmx, "unit": "solves/s", "ms_total": msmx,
+                                "form": "one ipi_solve per instance, mixed precision"}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, m_done, secs = oracle_batch_sample(syns)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+            "sample": (f"oracle iGMRES-PI (Alg. 2) solves of the batch's first {m_done} "
+                       f"instances ({secs:.1f} s of CPU); instances are i.i.d. draws")}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    b.close()
+    for h in hs:
+        h.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -255,6 +499,8 @@ def main():
     import paper_2211_04299_gb300 as mg
     import mdp_synth
 
+    if args.config == 4:
+        return run_batch_bench(args, mg, torch, dist, world, rank, local)
     if args.config != 2:
         scale = 1.0 if (args.config != 3 or args.S == S_) else args.S / 1_000_000
         syn = mdp_synth.config(args.config, scale=scale)
@@ -266,7 +512,8 @@ def main():
         syn = mdp_synth.dense_dirichlet(args.S, A_, 0.1, GAMMA, mdp_synth.CONFIG_SEEDS[2])
     S, A = syn.S, syn.A
     h = mg.from_synth(syn)
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # not the legacy default stream: see run_batch_bench
+    torch.cuda.set_stream(stream)
     h.set_stream(stream)
     o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
                 flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0)

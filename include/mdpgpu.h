@@ -274,6 +274,14 @@ int mdp_batch_solve(mdp_batch_t b, double* const* v_out, int32_t* const* pi_out,
                     mdp_stats* stats);
 int mdp_batch_solve_dev(mdp_batch_t b, double* const* v_out, int32_t* const* pi_out,
                         mdp_stats* stats);
+/* One Bellman sweep (Sec. 2, the operator T) of every instance at its current V, in one
+ * launch per lane class: after a solve V = V_K, so this recomputes T V_K, GreedyPolicy(V_K)
+ * and ||T V_K - V_K||_inf inside the batch's workspace.  res_inf: n host doubles, or NULL
+ * to return without waiting (the launches are then only enqueued on the batch's stream). */
+int mdp_batch_bellman(mdp_batch_t b, double* res_inf);
+/* opts->flags & MDP_FLAG_HOST_LOOP makes mdp_batch_solve enqueue the loop iterations from the
+ * host (one host wait per iteration) instead of launching one graph: same kernels, same
+ * results, visible to profilers that cannot follow conditional graph nodes. */
 /* One-shot form: create a batch of hs[0..n-1], solve into host buffers, destroy. */
 int ipi_solve_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, double* const* v_out,
                     int32_t* const* pi_out, mdp_stats* stats);

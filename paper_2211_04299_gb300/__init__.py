@@ -288,6 +288,16 @@ class MDPBatch:
     def device_bytes(self) -> int:
         return int(lib().mdp_batch_device_bytes(self.ptr))
 
+    def bellman(self, wait: bool = True):
+        """One Bellman sweep of every instance at its current V -> ||T V - V||_inf per
+        instance (wait=False only enqueues the launches and returns None)."""
+        if not wait:
+            _check(lib().mdp_batch_bellman(self.ptr, None), "mdp_batch_bellman")
+            return None
+        res = np.empty(self.n, dtype=np.float64)
+        _check(lib().mdp_batch_bellman(self.ptr, _ptr(res)), "mdp_batch_bellman")
+        return res
+
     def solve(self, v_out=None, pi_out=None, device: bool = False):
         """Solve every instance -> (list of v, list of pi, list of stats dicts, status)."""
         if v_out is None:

@@ -65,6 +65,7 @@ SIGNATURES = {
     "mdp_batch_tune": (C.c_int, [_h]),
     "mdp_batch_geometry": (C.c_int, [_h, C.c_int32, _ip, _ip, _ip, _ip, _ip]),
     "mdp_batch_device_bytes": (C.c_int64, [_h]),
+    "mdp_batch_bellman": (C.c_int, [_h, _vp]),
     "mdp_batch_solve": (C.c_int, [_h, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(mdp_stats)]),
     "mdp_batch_solve_dev": (C.c_int, [_h, C.POINTER(_vp), C.POINTER(_vp), C.POINTER(mdp_stats)]),
     "ipi_solve_batch": (C.c_int, [C.POINTER(_h), C.c_int32, C.POINTER(mdp_opts), C.POINTER(_vp), C.POINTER(_vp), C.POINTER(mdp_stats)]),

@@ -83,22 +83,18 @@ __device__ void build_list(const BatchList& L, int n, Pred pred, NB nbf) {
 }
 
 __device__ void build_sweep_lists(const BatchDev& B) {
-  for (int c = 0; c < BATCH_CLASSES; ++c)
-    build_list(
-        B.sw[c], B.n,
-        [&](int j) {
-          const BatchInst& I = B.insts[j];
-          return (I.phase == BP_SWEEP0 || I.phase == BP_SWEEPV) && I.cls_sw == c;
-        },
-        [&](int j) { return B.insts[j].nb_sw; });
+  build_list(
+      B.sw, B.n,
+      [&](int j) {
+        const BatchInst& I = B.insts[j];
+        return I.phase == BP_SWEEP0 || I.phase == BP_SWEEPV;
+      },
+      [&](int j) { return B.insts[j].nb_sw; });
 }
 
 __device__ void build_inner_lists(const BatchDev& B) {
-  for (int c = 0; c < BATCH_CLASSES; ++c)
-    build_list(
-        B.mv[c], B.n,
-        [&](int j) { return B.insts[j].phase == BP_INNER && B.insts[j].cls_mv == c; },
-        [&](int j) { return B.insts[j].nb_mv; });
+  build_list(B.mv, B.n, [&](int j) { return B.insts[j].phase == BP_INNER; },
+             [&](int j) { return B.insts[j].nb_mv; });
   build_list(B.ts, B.n, [&](int j) { return B.insts[j].phase == BP_INNER; },
              [&](int j) { return B.insts[j].nb_ts; });
   build_list(B.ew, B.n, [&](int j) { return B.insts[j].phase == BP_INNER; },
@@ -123,9 +119,8 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_init_kernel(BatchDev B) {
   }
   __syncthreads();
   build_sweep_lists(B);
-  for (int c = 0; c < BATCH_CLASSES; ++c)
-    if (threadIdx.x == 0) *B.mv[c].count = 0;
   if (threadIdx.x == 0) {
+    *B.mv.count = 0;
     *B.ts.count = 0;
     *B.ew.count = 0;
     B.ctr[0] = B.n;
@@ -237,7 +232,8 @@ __global__ void __launch_bounds__(EW_THREADS) batch_value_update_kernel(BatchDev
 // Loop condition: finished inner solves move to their verifying sweep; the WHILE node runs
 // again while some instance is not done (and the iteration guard allows).
 __global__ void __launch_bounds__(CTRL_THREADS) batch_loop_kernel(BatchDev B,
-                                                                  cudaGraphConditionalHandle hc) {
+                                                                  cudaGraphConditionalHandle hc,
+                                                                  int with_cond) {
   __shared__ int active;
   if (threadIdx.x == 0) active = 0;
   __syncthreads();
@@ -255,8 +251,17 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_loop_kernel(BatchDev B,
     B.ctr[0] = active;
     const bool more = active > 0 && it < B.max_iters;
     if (active > 0 && !more) B.ctr[2] = 1;
-    cudaGraphSetConditional(hc, more ? 1u : 0u);
+    B.ctr[3] = more ? 1 : 0;
+    if (with_cond) cudaGraphSetConditional(hc, more ? 1u : 0u);
   }
+}
+
+// One Bellman sweep of every instance at its current V (mdp_batch_bellman): every instance
+// gets phase SWEEP0 (its policy buffer pib[cur] receives GreedyPolicy(V)).
+__global__ void __launch_bounds__(CTRL_THREADS) batch_sweep_all_kernel(BatchDev B) {
+  for (int j = threadIdx.x; j < B.n; j += blockDim.x) B.insts[j].phase = BP_SWEEP0;
+  __syncthreads();
+  build_sweep_lists(B);
 }
 
 __global__ void __launch_bounds__(EW_THREADS) batch_zero_v_kernel(BatchDev B) {
@@ -314,7 +319,7 @@ struct mdp_batch_s {
   void** d_outp = nullptr;       // [2n] device pointer table (vout, pout)
   void** h_outp = nullptr;       // pinned staging
   BatchDev B{};
-  int grid_sw[BATCH_CLASSES] = {0}, grid_mv[BATCH_CLASSES] = {0};
+  int grid_sw = 0, grid_mv = 0;
   int grid_ts = 0, grid_ew = 0, grid_all = 0;
   int launches_per_iter = 0;
   cudaGraphExec_t exec = nullptr;
@@ -334,18 +339,20 @@ namespace {
     if (r_ != MDP_OK) return r_ == MDP_EDEVICE ? set_error(r_, #x) : r_;              \
   } while (0)
 
-// Virtual blocks per kernel family: a sweep block streams about 128 KB of P, a matvec block
-// about 64 KB, a Krylov block 2048 rows, an element-wise block 4096 rows.
+// Virtual blocks per kernel family: a sweep block streams about 512 KB of P, a matvec block
+// about 256 KB, a Krylov block 4096 rows, an element-wise block 8192 rows.  Each virtual
+// block ends with a block-wide reduction, so larger blocks amortise it; the batch supplies
+// the parallelism that small instances lack.
 void batch_geometry(const DevMDP& d, BatchInst& I) {
   const int64_t S = d.S;
   const int64_t row_b = (int64_t)d.kp * 8;
   auto clampb = [](int64_t x) { return (int)std::max<int64_t>(1, std::min<int64_t>(x, MAX_RED_BLOCKS)); };
-  const int64_t st_sw = std::max<int64_t>(8, 131072 / std::max<int64_t>(1, row_b * d.A));
-  const int64_t st_mv = std::max<int64_t>(32, 65536 / std::max<int64_t>(1, row_b));
+  const int64_t st_sw = std::max<int64_t>(8, 524288 / std::max<int64_t>(1, row_b * d.A));
+  const int64_t st_mv = std::max<int64_t>(32, 262144 / std::max<int64_t>(1, row_b));
   I.nb_sw = clampb((S + st_sw - 1) / st_sw);
   I.nb_mv = clampb((S + st_mv - 1) / st_mv);
-  I.nb_ts = clampb((S + 2047) / 2048);
-  I.nb_ew = clampb((S + 4095) / 4096);
+  I.nb_ts = clampb((S + 4095) / 4096);
+  I.nb_ew = clampb((S + 8191) / 8192);
 }
 
 void free_batch(mdp_batch_s* b) {
@@ -363,21 +370,17 @@ void free_batch(mdp_batch_s* b) {
 // Physical grids: the occupancy limit of each batched kernel, capped by the most virtual
 // blocks the family can have in one launch.
 void set_grids(mdp_batch_s* b) {
-  int64_t tsw[BATCH_CLASSES] = {0}, tmv[BATCH_CLASSES] = {0}, tts = 0, tew = 0;
+  int64_t tsw = 0, tmv = 0, tts = 0, tew = 0;
   for (const BatchInst& I : b->table) {
-    tsw[I.cls_sw] += I.nb_sw;
-    tmv[I.cls_mv] += I.nb_mv;
+    tsw += I.nb_sw;
+    tmv += I.nb_mv;
     tts += I.nb_ts;
     tew += I.nb_ew;
   }
-  // ctrl, prologue, three CGS2 kernels, estimate, value update, loop condition, plus one
-  // sweep per sweep class and two matvecs per matvec class present
-  b->launches_per_iter = 8;
-  for (int c = 0; c < BATCH_CLASSES; ++c) {
-    b->grid_sw[c] = tsw[c] ? (int)std::min<int64_t>(batch_sweep_grid(c), tsw[c]) : 0;
-    b->grid_mv[c] = tmv[c] ? (int)std::min<int64_t>(batch_matvec_grid(c), tmv[c]) : 0;
-    b->launches_per_iter += (tsw[c] ? 1 : 0) + (tmv[c] ? 2 : 0);
-  }
+  // sweep, ctrl, prologue, two matvecs, three CGS2 kernels, estimate, value update, loop
+  b->launches_per_iter = 11;
+  b->grid_sw = (int)std::max<int64_t>(1, std::min<int64_t>(batch_sweep_grid(), tsw));
+  b->grid_mv = (int)std::max<int64_t>(1, std::min<int64_t>(batch_matvec_grid(), tmv));
   b->grid_ts = (int)std::max<int64_t>(1, std::min<int64_t>(batch_ts_grid(b->o.restart + 1), tts));
   b->grid_ew = (int)std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms() * 8, tew));
   b->grid_all = b->grid_ew;
@@ -408,13 +411,44 @@ int upload_all_list(mdp_batch_s* b) {
   return MDP_OK;
 }
 
+// Kernels of the batch: the prologue (state reset, V_0 = 0), one loop iteration, and the
+// output conversion.  Every launch goes to stream st (a capturing stream when building the
+// graph).
+int enqueue_init(mdp_batch_s* b, cudaStream_t st) {
+  batch_init_kernel<<<1, CTRL_THREADS, 0, st>>>(b->B);
+  batch_zero_v_kernel<<<b->grid_all, EW_THREADS, 0, st>>>(b->B);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+int enqueue_iteration(mdp_batch_s* b, cudaStream_t st, cudaGraphConditionalHandle hc, int with_cond) {
+  const BatchDev& B = b->B;
+  const int maxm = b->o.restart + 1;
+  int r = launch_batch_sweep(B, b->grid_sw, st);
+  if (r != MDP_OK) return r;
+  batch_ctrl_kernel<<<1, CTRL_THREADS, 0, st>>>(B);
+  batch_prologue_kernel<<<b->grid_ew, EW_THREADS, 0, st>>>(B);
+  r = launch_batch_matvec(B, 0, b->grid_mv, st);
+  if (r == MDP_OK) r = launch_batch_cgs(B, maxm, b->grid_ts, st);
+  if (r == MDP_OK) r = launch_batch_estimate(B, maxm, b->grid_ts, st);
+  if (r == MDP_OK) r = launch_batch_matvec(B, 1, b->grid_mv, st);
+  if (r != MDP_OK) return r;
+  batch_value_update_kernel<<<b->grid_ew, EW_THREADS, 0, st>>>(B);
+  batch_loop_kernel<<<1, CTRL_THREADS, 0, st>>>(B, hc, with_cond);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+int enqueue_output(mdp_batch_s* b, cudaStream_t st) {
+  batch_output_kernel<<<b->grid_all, EW_THREADS, 0, st>>>(b->B);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+// The whole solve as one graph: prologue, WHILE node over one loop iteration, outputs.
 int build_graph(mdp_batch_s* b) {
   if (b->exec) {
     cudaGraphExecDestroy(b->exec);
     b->exec = nullptr;
   }
   if (!b->cap) BCK(cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking));
-  const BatchDev& B = b->B;
   cudaGraph_t g = nullptr;
   BCK(cudaGraphCreate(&g, 0));
   auto abort_capture = [&](const char* what) {
@@ -430,9 +464,7 @@ int build_graph(mdp_batch_s* b) {
   };
   if (cudaStreamBeginCaptureToGraph(b->cap, g, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return abort_capture("capture start");
-  batch_init_kernel<<<1, CTRL_THREADS, 0, b->cap>>>(B);
-  batch_zero_v_kernel<<<b->grid_all, EW_THREADS, 0, b->cap>>>(B);
-  if (cudaGetLastError() != cudaSuccess) return abort_capture("init launches");
+  if (enqueue_init(b, b->cap) != MDP_OK) return abort_capture("init launches");
   cudaStreamCaptureStatus cst;
   cudaGraph_t capg = nullptr;
   const cudaGraphNode_t* deps = nullptr;
@@ -453,32 +485,13 @@ int build_graph(mdp_batch_s* b) {
   cudaGraph_t body = np.conditional.phGraph_out[0];
   if (cudaStreamUpdateCaptureDependencies(b->cap, &cn, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
     return abort_capture("capture dependencies");
-  batch_output_kernel<<<b->grid_all, EW_THREADS, 0, b->cap>>>(B);
-  if (cudaGetLastError() != cudaSuccess) return abort_capture("output launch");
+  if (enqueue_output(b, b->cap) != MDP_OK) return abort_capture("output launch");
   cudaGraph_t g2 = nullptr;
   if (cudaStreamEndCapture(b->cap, &g2) != cudaSuccess) return abort_capture("end capture");
   // loop body: one iteration of every instance's state machine
   if (cudaStreamBeginCaptureToGraph(b->cap, body, nullptr, nullptr, 0, cudaStreamCaptureModeRelaxed) != cudaSuccess)
     return abort_capture("body capture start");
-  int r = MDP_OK;
-  const int maxm = b->o.restart + 1;
-  for (int c = 0; c < BATCH_CLASSES && r == MDP_OK; ++c)
-    if (b->grid_sw[c]) r = launch_batch_sweep(B, c, b->grid_sw[c], b->cap);
-  if (r == MDP_OK) {
-    batch_ctrl_kernel<<<1, CTRL_THREADS, 0, b->cap>>>(B);
-    batch_prologue_kernel<<<b->grid_ew, EW_THREADS, 0, b->cap>>>(B);
-  }
-  for (int c = 0; c < BATCH_CLASSES && r == MDP_OK; ++c)
-    if (b->grid_mv[c]) r = launch_batch_matvec(B, c, 0, b->grid_mv[c], b->cap);
-  if (r == MDP_OK) r = launch_batch_cgs(B, maxm, b->grid_ts, b->cap);
-  if (r == MDP_OK) r = launch_batch_estimate(B, maxm, b->grid_ts, b->cap);
-  for (int c = 0; c < BATCH_CLASSES && r == MDP_OK; ++c)
-    if (b->grid_mv[c]) r = launch_batch_matvec(B, c, 1, b->grid_mv[c], b->cap);
-  if (r == MDP_OK) {
-    batch_value_update_kernel<<<b->grid_ew, EW_THREADS, 0, b->cap>>>(B);
-    batch_loop_kernel<<<1, CTRL_THREADS, 0, b->cap>>>(B, hc);
-  }
-  if (r != MDP_OK || cudaGetLastError() != cudaSuccess) return abort_capture("body launches");
+  if (enqueue_iteration(b, b->cap, hc, 1) != MDP_OK) return abort_capture("body launches");
   cudaGraph_t b2 = nullptr;
   if (cudaStreamEndCapture(b->cap, &b2) != cudaSuccess) return abort_capture("end body capture");
   if (cudaGraphInstantiate(&b->exec, g, 0) != cudaSuccess) {
@@ -487,6 +500,19 @@ int build_graph(mdp_batch_s* b) {
   }
   cudaGraphDestroy(g);
   return MDP_OK;
+}
+
+// The same kernels enqueued from the host, one loop iteration at a time (the host reads
+// the loop condition after each), for tools that cannot follow conditional graph nodes.
+int run_host_loop(mdp_batch_s* b) {
+  BRK(enqueue_init(b, b->stream));
+  for (int it = 0; it < b->B.max_iters; ++it) {
+    BRK(enqueue_iteration(b, b->stream, 0, 0));
+    BCK(cudaMemcpyAsync(b->h_ctr, b->d_ctr, 4 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+    BCK(cudaStreamSynchronize(b->stream));
+    if (!b->h_ctr[3]) break;
+  }
+  return enqueue_output(b, b->stream);
 }
 
 int check_batch_opts(const mdp_opts& o) {
@@ -581,7 +607,7 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   // device tables
   BCK(cudaMalloc((void**)&b->d_insts, sizeof(BatchInst) * n));
   BCK(cudaMallocHost((void**)&b->h_insts, sizeof(BatchInst) * n));
-  const int nlists = 2 * BATCH_CLASSES + 3;
+  const int nlists = 5;
   const size_t per_list = (size_t)2 * n + 2;
   BCK(cudaMalloc((void**)&b->d_lists, sizeof(int) * per_list * nlists));
   BCK(cudaMemset(b->d_lists, 0, sizeof(int) * per_list * nlists));
@@ -602,13 +628,11 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   B.W = W;
   B.max_steps = b->o.max_inner;
   B.max_outer = b->o.max_outer;
-  for (int c = 0; c < BATCH_CLASSES; ++c) {
-    B.sw[c] = list_at(c);
-    B.mv[c] = list_at(BATCH_CLASSES + c);
-  }
-  B.ts = list_at(2 * BATCH_CLASSES);
-  B.ew = list_at(2 * BATCH_CLASSES + 1);
-  B.all = list_at(2 * BATCH_CLASSES + 2);
+  B.sw = list_at(0);
+  B.mv = list_at(1);
+  B.ts = list_at(2);
+  B.ew = list_at(3);
+  B.all = list_at(4);
   B.vout = (double**)b->d_outp;
   B.pout = (int32_t**)(b->d_outp + n);
   B.ctr = b->d_ctr;
@@ -631,9 +655,11 @@ int run_batch(mdp_batch_s* b, double* const* v_out, int32_t* const* pi_out, mdp_
     b->h_outp[j] = device_out ? (void*)v_out[j] : (void*)(b->outpool + b->vo_off[j]);
     b->h_outp[n + j] = device_out ? (void*)pi_out[j] : (void*)(b->outpool + b->po_off[j]);
   }
-  if (!b->exec) BRK(build_graph(b));
+  const bool host_loop = (b->o.flags & MDP_FLAG_HOST_LOOP) != 0;
+  if (!host_loop && !b->exec) BRK(build_graph(b));
   BCK(cudaMemcpyAsync(b->d_outp, b->h_outp, sizeof(void*) * 2 * n, cudaMemcpyHostToDevice, b->stream));
-  BCK(cudaGraphLaunch(b->exec, b->stream));
+  if (host_loop) BRK(run_host_loop(b));
+  else BCK(cudaGraphLaunch(b->exec, b->stream));
   BCK(cudaMemcpyAsync(b->h_ctr, b->d_ctr, 3 * sizeof(int), cudaMemcpyDeviceToHost, b->stream));
   BCK(cudaMemcpyAsync(b->h_insts, b->d_insts, sizeof(BatchInst) * n, cudaMemcpyDeviceToHost, b->stream));
   if (!device_out) {
@@ -711,11 +737,11 @@ int tune_batch(mdp_batch_s* b) {
   std::vector<int> kps;
   for (const BatchInst& I : b->table)
     if (std::find(kps.begin(), kps.end(), I.d.kp) == kps.end()) kps.push_back(I.d.kp);
+  std::vector<BatchInst> saved = b->table;
   for (BatchInst& I : b->table) {  // tuning launches run ungated: a valid phase and policy
     I.phase = BP_SWEEP0;
     I.cur = 0;
   }
-  BRK(upload_table(b));
   for (int kp : kps) {
     std::vector<int> ids;
     for (int j = 0; j < b->n; ++j)
@@ -723,31 +749,34 @@ int tune_batch(mdp_batch_s* b) {
     for (int fam = 0; fam < 2; ++fam) {
       float best = 1e30f;
       int best_c = 0;
+      const BatchList& L = fam == 0 ? b->B.sw : b->B.mv;
+      BRK(upload_list(b, L, ids, fam == 0));
+      int64_t tot = 0;
+      for (int j : ids) tot += fam == 0 ? b->table[j].nb_sw : b->table[j].nb_mv;
+      const int grid = (int)std::min<int64_t>(fam == 0 ? batch_sweep_grid() : batch_matvec_grid(), tot);
       for (int c = 0; c < BATCH_CLASSES; ++c) {
-        const BatchList& L = fam == 0 ? b->B.sw[c] : b->B.mv[c];
-        BRK(upload_list(b, L, ids, fam == 0));
-        int64_t tot = 0;
-        for (int j : ids) tot += fam == 0 ? b->table[j].nb_sw : b->table[j].nb_mv;
-        const int grid = (int)std::min<int64_t>(fam == 0 ? batch_sweep_grid(c) : batch_matvec_grid(c), tot);
+        for (int j : ids) (fam == 0 ? b->table[j].cls_sw : b->table[j].cls_mv) = c;
+        BRK(upload_table(b));
         int r = MDP_OK;
         const float ms = time_best(b, [&]() {
           if (r != MDP_OK) return;
-          r = fam == 0 ? launch_batch_sweep(b->B, c, grid, b->stream)
-                       : launch_batch_matvec(b->B, c, 2, grid, b->stream);
+          r = fam == 0 ? launch_batch_sweep(b->B, grid, b->stream)
+                       : launch_batch_matvec(b->B, 2, grid, b->stream);
         });
         BRK(r);
         BCK(cudaGetLastError());
-        const int empty = 0;
-        BCK(cudaMemcpy(L.count, &empty, sizeof(int), cudaMemcpyHostToDevice));
         if (ms < best) {
           best = ms;
           best_c = c;
         }
       }
+      const int empty = 0;
+      BCK(cudaMemcpy(L.count, &empty, sizeof(int), cudaMemcpyHostToDevice));
+      for (int j : ids) (fam == 0 ? saved[j].cls_sw : saved[j].cls_mv) = best_c;
       for (int j : ids) (fam == 0 ? b->table[j].cls_sw : b->table[j].cls_mv) = best_c;
     }
   }
-  for (BatchInst& I : b->table) I.phase = BP_DONE;
+  b->table = saved;
   BRK(upload_table(b));
   set_grids(b);
   if (b->exec) {
@@ -808,6 +837,24 @@ int mdp_batch_geometry(mdp_batch_t b, int32_t i, int32_t* lanes_sweep, int32_t* 
 int64_t mdp_batch_device_bytes(mdp_batch_t b) {
   if (!b) return 0;
   return (int64_t)(b->pool_bytes + b->out_bytes);
+}
+
+int mdp_batch_bellman(mdp_batch_t b, double* res_inf) {
+  if (!b) return set_error(MDP_EINVAL, "null batch");
+  batch_sweep_all_kernel<<<1, CTRL_THREADS, 0, b->stream>>>(b->B);
+  BCK(cudaGetLastError());
+  BRK(launch_batch_sweep(b->B, b->grid_sw, b->stream));
+  if (!res_inf) return MDP_OK;
+  BCK(cudaMemcpyAsync(b->h_insts, b->d_insts, sizeof(BatchInst) * b->n, cudaMemcpyDeviceToHost,
+                      b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  std::vector<SweepOut> so(b->n);
+  for (int j = 0; j < b->n; ++j)
+    BCK(cudaMemcpyAsync(&so[j], b->h_insts[j].sout, sizeof(SweepOut), cudaMemcpyDeviceToHost,
+                        b->stream));
+  BCK(cudaStreamSynchronize(b->stream));
+  for (int j = 0; j < b->n; ++j) res_inf[j] = so[j].res_inf;
+  return MDP_OK;
 }
 
 int mdp_batch_solve(mdp_batch_t b, double* const* v_out, int32_t* const* pi_out, mdp_stats* stats) {

@@ -1071,13 +1071,19 @@ __device__ __forceinline__ MatvecK batch_matvec_params(const BatchInst& I, int w
   return p;
 }
 
-template <int T>
-__global__ void __launch_bounds__(256) batch_matvec_kernel(BatchDev B, int cls, int which) {
+__global__ void __launch_bounds__(256) batch_matvec_kernel(BatchDev B, int which) {
   __shared__ MatvecK mp;
-  batch_for_each(B.mv[cls], [&](int j, GridPos gp) {
-    if (threadIdx.x == 0) mp = batch_matvec_params(B.insts[j], which);
+  __shared__ BatchInst si;
+  batch_for_each(B.mv, [&](int j, GridPos gp) {
+    batch_stage_inst(B.insts + j, &si);
+    if (threadIdx.x == 0) mp = batch_matvec_params(si, which);
     __syncthreads();
-    matvec_ell_body<float, float, T>(mp, gp);
+    switch (si.cls_mv) {
+      case 0: matvec_ell_body<float, float, 1>(mp, gp); break;
+      case 1: matvec_ell_body<float, float, 2>(mp, gp); break;
+      case 2: matvec_ell_body<float, float, 4>(mp, gp); break;
+      default: matvec_ell_body<float, float, 8>(mp, gp); break;
+    }
   });
 }
 
@@ -1088,8 +1094,10 @@ __device__ __forceinline__ KB batch_kb(const BatchInst& I) {
 template <int MAXM, int STAGE>
 __global__ void __launch_bounds__(RED_THREADS) batch_ts_kernel(BatchDev B) {
   __shared__ KB kb;
+  __shared__ BatchInst si;
   batch_for_each(B.ts, [&](int j, GridPos gp) {
-    if (threadIdx.x == 0) kb = batch_kb(B.insts[j]);
+    batch_stage_inst(B.insts + j, &si);
+    if (threadIdx.x == 0) kb = batch_kb(si);
     __syncthreads();
     if (STAGE == 0) cgs_dots_body<float, MAXM>(kb, gp);
     else if (STAGE == 1) cgs_axpy_dots_body<float, MAXM>(kb, gp);
@@ -1161,27 +1169,17 @@ int krylov_blocks(int64_t S) {
   return (int)std::max<int64_t>(1, std::min<int64_t>(g, MAX_RED_BLOCKS));
 }
 
-int batch_matvec_grid(int cls) {
+int batch_matvec_grid() {
   int per_sm = 1;
-  cudaError_t e = cudaSuccess;
-  switch (cls) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<1>, 256, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<2>, 256, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<4>, 256, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel<8>, 256, 0); break;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_matvec_kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
   }
-  if (e != cudaSuccess) { cudaGetLastError(); per_sm = 1; }
   return num_sms() * std::max(per_sm, 1);
 }
 
-int launch_batch_matvec(const BatchDev& B, int cls, int which, int grid, cudaStream_t st) {
-  switch (cls) {
-    case 0: batch_matvec_kernel<1><<<grid, 256, 0, st>>>(B, cls, which); break;
-    case 1: batch_matvec_kernel<2><<<grid, 256, 0, st>>>(B, cls, which); break;
-    case 2: batch_matvec_kernel<4><<<grid, 256, 0, st>>>(B, cls, which); break;
-    case 3: batch_matvec_kernel<8><<<grid, 256, 0, st>>>(B, cls, which); break;
-    default: return MDP_EINVAL;
-  }
+int launch_batch_matvec(const BatchDev& B, int which, int grid, cudaStream_t st) {
+  batch_matvec_kernel<<<grid, 256, 0, st>>>(B, which);
   return ok_or_dev();
 }
 

@@ -527,8 +527,8 @@ struct BatchDev {
   int n;
   double alpha, tol;
   int W, max_steps, max_outer;
-  BatchList sw[BATCH_CLASSES];  // sweeps due (by sweep lane class)
-  BatchList mv[BATCH_CLASSES];  // inner solves running (by matvec lane class)
+  BatchList sw;                 // sweeps due
+  BatchList mv;                 // inner solves running (matvec blocks)
   BatchList ts;                 // inner solves running (tall-skinny kernels)
   BatchList ew;                 // inner solves running (element-wise kernels)
   BatchList all;                // every instance (element-wise kernels)
@@ -548,6 +548,17 @@ __device__ __forceinline__ int batch_slot(const int* first, int cnt, int vb) {
   return lo;
 }
 
+// Copy an instance record into shared memory with every thread of the block (one word per
+// thread, so the loads overlap), then wait for the copy.
+__device__ __forceinline__ void batch_stage_inst(const BatchInst* g, BatchInst* s) {
+  static_assert(sizeof(BatchInst) % 4 == 0, "BatchInst is copied in 4-byte words");
+  constexpr int NW = (int)(sizeof(BatchInst) / 4);
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(g);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(s);
+  for (int i = threadIdx.x; i < NW; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
+
 // Run f(instance, GridPos) for every virtual block of list L (grid-stride over blocks).
 template <class F>
 __device__ __forceinline__ void batch_for_each(const BatchList& L, F&& f) {
@@ -562,12 +573,14 @@ __device__ __forceinline__ void batch_for_each(const BatchList& L, F&& f) {
   }
 }
 
-// Batched kernel families (sweep.cu, krylov.cu).  grid = physical blocks.
-int launch_batch_sweep(const BatchDev& B, int cls, int grid, cudaStream_t st);
-int batch_sweep_grid(int cls);
+// Batched kernel families (sweep.cu, krylov.cu).  grid = physical blocks.  Each virtual
+// block runs the kernel body for its instance's lane count (cls_sw / cls_mv), so one launch
+// serves instances of every shape.
+int launch_batch_sweep(const BatchDev& B, int grid, cudaStream_t st);
+int batch_sweep_grid();
 // which: 0 Arnoldi-step matvec, 1 true-residual matvec (CHECK / RESTART), 2 timing only
-int launch_batch_matvec(const BatchDev& B, int cls, int which, int grid, cudaStream_t st);
-int batch_matvec_grid(int cls);
+int launch_batch_matvec(const BatchDev& B, int which, int grid, cudaStream_t st);
+int batch_matvec_grid();
 int launch_batch_cgs(const BatchDev& B, int maxm, int grid, cudaStream_t st);
 int launch_batch_estimate(const BatchDev& B, int maxm, int grid, cudaStream_t st);
 int batch_ts_grid(int maxm);

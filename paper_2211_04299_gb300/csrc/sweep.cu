@@ -788,16 +788,17 @@ __global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
   sweep_ell_body<PT, AR, T>(p, this_grid());
 }
 
-// Batched sweep: the virtual blocks of every instance whose sweep is due (class cls).  The
-// launch parameters of an instance are staged in shared memory by thread 0.  Phase SWEEP0
+// Batched sweep: the virtual blocks of every instance whose sweep is due.  The instance
+// record is staged in shared memory; thread 0 assembles the launch parameters.  Phase SWEEP0
 // writes pi_k; phase SWEEPV writes the candidate pi_{k+1} into the other policy buffer and
 // the exact residual of pi_k (the reference policy) into rref.
-template <int T>
-__global__ void __launch_bounds__(256, 3) batch_sweep_kernel(BatchDev B, int cls) {
+__global__ void __launch_bounds__(256, 3) batch_sweep_kernel(BatchDev B) {
   __shared__ SweepK sp;
-  batch_for_each(B.sw[cls], [&](int j, GridPos gp) {
+  __shared__ BatchInst si;
+  batch_for_each(B.sw, [&](int j, GridPos gp) {
+    batch_stage_inst(B.insts + j, &si);
     if (threadIdx.x == 0) {
-      const BatchInst& I = B.insts[j];
+      const BatchInst& I = si;
       const bool verify = I.phase == BP_SWEEPV;
       SweepK p;
       p.d = I.d;
@@ -817,7 +818,12 @@ __global__ void __launch_bounds__(256, 3) batch_sweep_kernel(BatchDev B, int cls
       sp = p;
     }
     __syncthreads();
-    sweep_ell_body<float, ArDF, T>(sp, gp);
+    switch (si.cls_sw) {
+      case 0: sweep_ell_body<float, ArDF, 1>(sp, gp); break;
+      case 1: sweep_ell_body<float, ArDF, 2>(sp, gp); break;
+      case 2: sweep_ell_body<float, ArDF, 4>(sp, gp); break;
+      default: sweep_ell_body<float, ArDF, 8>(sp, gp); break;
+    }
   });
 }
 
@@ -897,27 +903,17 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
 
 int ell_sweep_lanes_default(const DevMDP& d) { return (d.kp / 4) >= 8 ? 2 : 1; }
 
-int batch_sweep_grid(int cls) {
+int batch_sweep_grid() {
   int per_sm = 1;
-  cudaError_t e = cudaSuccess;
-  switch (cls) {
-    case 0: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<1>, 256, 0); break;
-    case 1: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<2>, 256, 0); break;
-    case 2: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<4>, 256, 0); break;
-    default: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel<8>, 256, 0); break;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_sweep_kernel, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    per_sm = 1;
   }
-  if (e != cudaSuccess) { cudaGetLastError(); per_sm = 1; }
   return num_sms() * std::max(per_sm, 1);
 }
 
-int launch_batch_sweep(const BatchDev& B, int cls, int grid, cudaStream_t st) {
-  switch (cls) {
-    case 0: batch_sweep_kernel<1><<<grid, 256, 0, st>>>(B, cls); break;
-    case 1: batch_sweep_kernel<2><<<grid, 256, 0, st>>>(B, cls); break;
-    case 2: batch_sweep_kernel<4><<<grid, 256, 0, st>>>(B, cls); break;
-    case 3: batch_sweep_kernel<8><<<grid, 256, 0, st>>>(B, cls); break;
-    default: return MDP_EINVAL;
-  }
+int launch_batch_sweep(const BatchDev& B, int grid, cudaStream_t st) {
+  batch_sweep_kernel<<<grid, 256, 0, st>>>(B);
   return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
 }
 

@@ -238,3 +238,24 @@ def test_config4_full_size_sampled(mg):
         ref = oracle.policy_iteration(m, tol=1e-11)
         assert rel_err(vs[i], ref.v) <= 1e-6
         check_policy(ps[i], oracle.bellman(m, ref.v))
+
+
+def test_host_loop_equals_graph_and_batched_bellman(mg):
+    """The host-driven loop runs the same kernels as the graph (results equal bit for bit);
+    the batched Bellman sweep at the final V_K reproduces each instance's ||Phi_K||_inf."""
+    specs = scaled_specs(7, 13, 0.1)
+    syns, hs = handles_for(mg, specs)
+    vs, ps, sts, _ = mg.MDPBatch(hs, mg.opts(**OPTS)).solve()
+    hb = mg.MDPBatch(hs, mg.opts(flags=mg.MDP_FLAG_HOST_LOOP, **OPTS))
+    vs2, ps2, sts2, code = hb.solve()
+    assert code == 0
+    for i in range(len(hs)):
+        np.testing.assert_array_equal(vs2[i], vs[i])
+        np.testing.assert_array_equal(ps2[i], ps[i])
+        assert sts2[i]["inner"] == sts[i]["inner"]
+    res = hb.bellman()
+    np.testing.assert_array_equal(res, [s["residual_inf"] for s in sts2])
+    for syn, v, r in zip(syns, vs2, res):
+        m = oracle.from_synth(syn)
+        # v = T(V_K): the oracle's residual at v is at most gamma * ||Phi_K||_inf (contraction)
+        assert oracle.bellman(m, v).res_inf <= syn.gamma * r * 1.01 + 1e-12
