@@ -51,10 +51,15 @@ def parse():
     ap.add_argument("--S", type=int, default=S_,
                     help="states of the dense (or, with --config 3, banded) workload; other "
                          "values only for profiling")
-    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4],
+    ap.add_argument("--duration", type=float, default=60.0,
+                    help="serving workload: seconds of the Poisson request trace")
+    ap.add_argument("--pool", type=int, default=64,
+                    help="serving workload: distinct MDPs the requests draw from")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3, 4, 5],
                     help="workload: 2 = the paper-scale dense MDP (the benchmark), 1 = small "
                          "ELL, 3 = S=10^6 banded ELL (for measurement of the ELL kernels), "
-                         "4 = a batch of 256 independent ELL MDPs solved together")
+                         "4 = a batch of 256 independent ELL MDPs solved together, "
+                         "5 = a Poisson stream of requests served with continuous batching")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workload: keep the library's lanes per row (no autotuning), "
@@ -481,6 +486,181 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     return 0
 
 
+# ---------------------------------------------------------------- serving workload
+SERVE_WORKLOAD = ("Poisson stream of solve requests at 200/s for {dur:g} s ({n} requests): ELL "
+                  "MDPs with S log-uniform in [1e3, 2e5], A in {{4, 8, 16}}, k=16, gamma in "
+                  "{{0.95, 0.99}}, FP32 values, g~U(0,1), drawn from {pool} distinct seeded "
+                  "instances; iGMRES-PI mixed, alpha=0.1, W=30, tol 1e-8; continuous batching "
+                  "with a 120 GB HBM budget; each request uploads its P and g from pinned host "
+                  "memory and copies v, pi back")
+
+
+def serve_trace(args):
+    import mdp_synth
+    trace = mdp_synth.serving_trace(200.0, args.duration, mdp_synth.CONFIG_SEEDS[5])
+    npool = min(args.pool, len(trace))
+    return trace, npool
+
+
+def replay(trace, npool, submit, poll, idle_wait=0.0002):
+    """Submit request j at trace[j]['t'] (seconds after start) -> per-request latency (s),
+    wall time from the first arrival to the last completion."""
+    n = len(trace)
+    arrive = {}
+    lat = {}
+    t0 = time.perf_counter()
+    nxt = 0
+    while len(lat) < n:
+        now = time.perf_counter() - t0
+        while nxt < n and trace[nxt]["t"] <= now:
+            rid = submit(nxt, nxt % npool)
+            arrive[rid] = t0 + trace[nxt]["t"]
+            nxt += 1
+        done = poll()
+        t = time.perf_counter()
+        for rid, status in done:
+            lat[rid] = (t - arrive[rid], status)
+        if not done and nxt < n:
+            time.sleep(idle_wait)
+    t_end = time.perf_counter()
+    return lat, t_end - (t0 + trace[0]["t"])
+
+
+def run_serve_bench(args, mg, torch, dist, world, rank, local):
+    import mdp_synth
+    trace, npool = serve_trace(args)
+    n = len(trace)
+    pool = [mdp_synth.instance_from_spec(sp) for sp in trace[:npool]]
+    pinned = [(torch.from_numpy(np.ascontiguousarray(p.col)).pin_memory().numpy(),
+               torch.from_numpy(np.ascontiguousarray(p.val)).pin_memory().numpy(),
+               torch.from_numpy(np.ascontiguousarray(p.g)).pin_memory().numpy()) for p in pool]
+    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed")
+    srv = mg.MDPServer(o=o, hbm_budget_bytes=120 << 30)
+    statuses = []
+
+    def submit(j, pi):
+        c, v, g = pinned[pi]
+        return srv.submit(c, v, g, pool[pi].gamma)
+
+    def poll():
+        out = []
+        for rid, _, _, st in srv.poll():
+            out.append((rid, st["status"]))
+            statuses.append(st)
+        return out
+
+    # warm-up: the first pool instances once each
+    for j in range(min(8, npool)):
+        submit(j, j)
+    srv.drain()
+    srv.poll()
+    statuses.clear()
+    l0 = srv.info()["launches"]
+    clocks = Clocks(local)
+    clocks.start()
+    lat, wall = replay(trace, npool, submit, poll)
+    clk = clocks.stop()
+    launches = srv.info()["launches"] - l0
+    lats = np.array([x[0] for x in lat.values()]) * 1000.0
+    ok = all(x[1] == 0 for x in lat.values())
+    value = n / wall
+
+    # capacity: the same requests all submitted at once
+    sat_n = min(n, 1000)
+    t0 = time.perf_counter()
+    for j in range(sat_n):
+        submit(j, j % npool)
+    srv.drain()
+    srv.poll()
+    sat = sat_n / (time.perf_counter() - t0)
+    srv.close()
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
+        "steps": n, "warmup": min(8, npool), "ms_per_step": 1000.0 * wall / n,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "mixed: f32 P/Krylov, double-float (2xf32) values, f64 Givens",
+        "data": "synthetic",
+        "config": {"workload": SERVE_WORKLOAD.format(dur=args.duration, n=n, pool=npool),
+                   "requests": n, "rate_per_s": 200.0, "duration_s": args.duration,
+                   "distinct_mdps": npool, "hbm_budget_gb": 120, "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 in aggregate; no flush"},
+        "step": "one request (arrival to result on the host)",
+        "converged": ok,
+        "latency_ms": {"p50": float(np.percentile(lats, 50)), "p99": float(np.percentile(lats, 99)),
+                       "max": float(lats.max())},
+        "capacity": {"value": sat, "unit": "solves/s", "requests": sat_n,
+                     "form": "the trace's first requests submitted at once"},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+        "e2e": {"value": value, "unit": "solves/s",
+                "h2d_bytes_per_step": int(np.mean([p.col.nbytes + p.val.nbytes + p.g.nbytes for p in pool])),
+                "d2h_bytes_per_step": int(np.mean([p.S * 12 for p in pool])),
+                "note": "the serving loop is end to end: uploads and result copies are inside"},
+        "roofline": None,
+    }
+
+    if not args.no_fp64:
+        # the plain FP64 per-request path on the same trace: one request after another, each
+        # uploading its (FP64) data into a handle of its shape and solving it alone
+        hs64 = []
+        for p in pool:
+            syn64 = mdp_synth.SynthMDP(S=p.S, A=p.A, gamma=p.gamma, g=p.g, kind="ell",
+                                       col=p.col, val=p.val.astype(np.float64))
+            hs64.append((mg.from_synth(syn64),
+                         torch.from_numpy(np.ascontiguousarray(syn64.val)).pin_memory().numpy()))
+        o64 = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="fp64")
+        queue = []
+        results = []
+        rid_next = [0]
+
+        def submit64(j, pi):
+            rid_next[0] += 1
+            queue.append((rid_next[0], pi))
+            return rid_next[0]
+
+        def poll64():
+            if not queue:
+                return []
+            rid, pi = queue.pop(0)
+            h, val64 = hs64[pi]
+            c, _, g = pinned[pi]
+            mg.mdp_load_ell(h, c, val64, g)
+            v = np.empty(pool[pi].S)
+            pi_o = np.empty(pool[pi].S, np.int32)
+            _, _, st = mg.ipi_solve(h, o64, v_out=v, pi_out=pi_o)
+            return [(rid, st["status"])]
+
+        lat64, wall64 = replay(trace, npool, submit64, poll64)
+        l64 = np.array([x[0] for x in lat64.values()]) * 1000.0
+        line["fp64_plain"] = {"value": n / wall64, "unit": "solves/s",
+                              "latency_ms": {"p50": float(np.percentile(l64, 50)),
+                                             "p99": float(np.percentile(l64, 99))},
+                              "form": "one request after another: mdp_load_ell + ipi_solve FP64"}
+        for h, _ in hs64:
+            h.close()
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        t_tot, m_done = 0.0, 0
+        for p in pool:
+            m = oracle.from_synth(p)
+            t0 = time.perf_counter()
+            oracle.gmres_policy_iteration(m, alpha=ALPHA, W=W_, tol=TOL)
+            t_tot += time.perf_counter() - t0
+            m_done += 1
+            if t_tot >= 12.0:
+                break
+        line["cpu_baseline"] = {
+            "value": m_done / t_tot, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+            "sample": f"oracle iGMRES-PI solves of the first {m_done} distinct request MDPs ({t_tot:.1f} s)"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
@@ -501,6 +681,8 @@ def main():
 
     if args.config == 4:
         return run_batch_bench(args, mg, torch, dist, world, rank, local)
+    if args.config == 5:
+        return run_serve_bench(args, mg, torch, dist, world, rank, local)
     if args.config != 2:
         scale = 1.0 if (args.config != 3 or args.S == S_) else args.S / 1_000_000
         syn = mdp_synth.config(args.config, scale=scale)

@@ -286,6 +286,49 @@ int mdp_batch_bellman(mdp_batch_t b, double* res_inf);
 int ipi_solve_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, double* const* v_out,
                     int32_t* const* pi_out, mdp_stats* stats);
 
+/* ---------------------------------------------------------------------------- serving */
+/* A server solves a stream of requests with continuous batching: each request is an ELL MDP
+ * with FP32 transition data, solved by iGMRES-PI (Alg. 2, mixed precision) from V_0 = 0.
+ * Admitted requests keep P, g, V, pi and the Krylov basis resident on the device; the
+ * device runs the batch engine's loop (see mdp_batch_*) over every active slot, in launches
+ * of iters_per_launch iterations, and between launches the host retires finished requests
+ * and activates newly uploaded ones, so requests that arrive while others are solving join
+ * the running mix.  A request is admitted (in arrival order) when a slot is free and its
+ * device bytes fit in the HBM budget together with every other admitted request.  Each
+ * result equals that of the same MDP solved alone (ipi_solve with the batch engine's kernel
+ * shape, see mdp_batch_geometry): the slots never exchange data.
+ * A server is used by one host thread at a time; it never blocks on the device except in
+ * mdp_server_drain. */
+typedef struct mdp_server_s* mdp_server_t;
+typedef struct {
+  int64_t hbm_budget_bytes; /* device bytes of all admitted requests together (default 120 GiB) */
+  int32_t max_slots;        /* requests on the device at once (1..4096, default 256) */
+  int32_t iters_per_launch; /* loop iterations per device launch (default 4) */
+  mdp_opts solver;          /* shared solver options: precision MIXED, v0 NULL, 0 < alpha < 1 */
+} mdp_server_opts;
+mdp_server_opts mdp_server_opts_default(void);
+int mdp_server_create(const mdp_server_opts* opts, mdp_server_t* out);
+void mdp_server_destroy(mdp_server_t s);  /* waits for the device, drops unfinished requests */
+/* Queue one request.  col / val [A][S][k] (int32 / FP32), g [A][S] (FP64): host arrays
+ * (pinned memory keeps the upload asynchronous).  v_out (S doubles) and pi_out (S ints):
+ * host or device buffers that receive T(V_K) and pi_K.  Every array must stay valid until
+ * the request is reported done.  *request_id (may be NULL) identifies it in poll results.
+ * Invalid data (found on the device) completes the request with status MDP_EINVAL; a request
+ * larger than the whole budget completes with MDP_ENOMEM. */
+int mdp_server_submit(mdp_server_t s, int64_t S, int32_t A, int32_t k, const int32_t* col,
+                      const float* val, const double* g, double gamma, double* v_out,
+                      int32_t* pi_out, int64_t* request_id);
+/* Advance the server without waiting (retire, admit, activate, launch) and report up to
+ * max_done completed requests: ids[i] and stats[i] (status, outer/inner counts, residual,
+ * seconds = submit-to-completion latency).  ids / stats may be NULL. */
+int mdp_server_poll(mdp_server_t s, int64_t* ids, mdp_stats* stats, int32_t max_done,
+                    int32_t* n_done);
+/* Run until every submitted request has completed (results stay queued for poll). */
+int mdp_server_drain(mdp_server_t s);
+/* Requests holding a slot, requests waiting, device bytes admitted, loop launches so far. */
+int mdp_server_info(mdp_server_t s, int32_t* active, int32_t* pending, int64_t* bytes_in_use,
+                    int64_t* launches);
+
 /* Message for the last nonzero return on this thread ("" if none). */
 const char* mdp_last_error(void);
 

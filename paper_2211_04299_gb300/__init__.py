@@ -13,12 +13,12 @@ import numpy as np
 
 from . import _lib
 from ._lib import (MDP_F32, MDP_F64, MDP_FLAG_HOST_LOOP, MDP_PREC_FP64,  # noqa: F401
-                   MDP_PREC_MIXED, MDPError, mdp_opts, mdp_stats)
+                   MDP_PREC_MIXED, MDPError, mdp_opts, mdp_server_opts, mdp_stats)
 
 __all__ = [
     "MDPHandle", "mdp_create_dense", "mdp_create_ell", "bellman_apply", "policy_eval_gmres",
     "ipi_solve", "vi_solve", "pi_solve", "opi_solve", "opts", "MDP_PREC_FP64",
-    "MDPBatch", "ipi_solve_batch",
+    "MDPBatch", "ipi_solve_batch", "MDPServer",
     "MDP_PREC_MIXED", "MDPError", "lib",
 ]
 
@@ -325,3 +325,86 @@ def ipi_solve_batch(handles, o=None):
     o = o or opts()
     code = _check(lib().ipi_solve_batch(arr, n, C.byref(o), vp, pp, st), "ipi_solve_batch")
     return vs, ps, [s.as_dict() for s in st], code
+
+
+class MDPServer:
+    """mdp_server_t: continuous batching of iGMRES-PI requests (mixed precision).
+
+    submit() takes ELL data as arrays col/val [A, S, k] (int32 / float32), g [A, S]
+    (float64) and output buffers; every array must stay alive (the object keeps references)
+    until the request is reported by poll()/drain()."""
+
+    def __init__(self, hbm_budget_bytes=None, max_slots=None, iters_per_launch=None, o=None):
+        so = lib().mdp_server_opts_default()
+        if hbm_budget_bytes is not None:
+            so.hbm_budget_bytes = int(hbm_budget_bytes)
+        if max_slots is not None:
+            so.max_slots = int(max_slots)
+        if iters_per_launch is not None:
+            so.iters_per_launch = int(iters_per_launch)
+        if o is not None:
+            so.solver = o
+        self._p = C.c_void_p()
+        _check(lib().mdp_server_create(C.byref(so), C.byref(self._p)), "mdp_server_create")
+        self._keep = {}
+        self.results = {}
+
+    @property
+    def ptr(self):
+        if self._p is None:
+            raise ValueError("server is closed")
+        return self._p
+
+    def close(self):
+        if self._p is not None:
+            lib().mdp_server_destroy(self._p)
+            self._p = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def submit(self, col, val, g, gamma, v_out=None, pi_out=None) -> int:
+        A, S, k = val.shape
+        if v_out is None:
+            v_out = np.empty(S, dtype=np.float64)
+        if pi_out is None:
+            pi_out = np.empty(S, dtype=np.int32)
+        rid = C.c_int64()
+        _check(lib().mdp_server_submit(self.ptr, S, A, k, _ptr(col), _ptr(val), _ptr(g),
+                                       float(gamma), _ptr(v_out), _ptr(pi_out), C.byref(rid)),
+               "mdp_server_submit")
+        self._keep[rid.value] = (col, val, g, v_out, pi_out)
+        return rid.value
+
+    def poll(self, max_done: int = 1024):
+        """Advance; returns [(id, v, pi, stats dict)] of the requests completed since."""
+        ids = (C.c_int64 * max_done)()
+        st = (mdp_stats * max_done)()
+        n = C.c_int32()
+        _check(lib().mdp_server_poll(self.ptr, ids, st, max_done, C.byref(n)), "mdp_server_poll")
+        out = []
+        for i in range(n.value):
+            _, _, _, v, pi = self._keep.pop(ids[i])
+            out.append((ids[i], v, pi, st[i].as_dict()))
+        return out
+
+    def drain(self):
+        """Run until every submitted request completed -> the poll() list of all of them."""
+        _check(lib().mdp_server_drain(self.ptr), "mdp_server_drain")
+        out = []
+        while True:
+            part = self.poll()
+            out.extend(part)
+            if not part:
+                break
+        return out
+
+    def info(self) -> dict:
+        a, p, b, l = C.c_int32(), C.c_int32(), C.c_int64(), C.c_int64()
+        _check(lib().mdp_server_info(self.ptr, C.byref(a), C.byref(p), C.byref(b), C.byref(l)),
+               "mdp_server_info")
+        return {"active": a.value, "pending": p.value, "bytes_in_use": b.value, "launches": l.value}

@@ -26,6 +26,11 @@ class mdp_opts(C.Structure):
                 ("v0", C.POINTER(C.c_double))]
 
 
+class mdp_server_opts(C.Structure):
+    _fields_ = [("hbm_budget_bytes", C.c_int64), ("max_slots", C.c_int32),
+                ("iters_per_launch", C.c_int32), ("solver", mdp_opts)]
+
+
 class mdp_stats(C.Structure):
     _fields_ = [("outer", C.c_int32), ("inner", C.c_int32), ("restarts", C.c_int32),
                 ("sweeps", C.c_int32), ("matvecs", C.c_int32), ("status", C.c_int32),
@@ -82,6 +87,13 @@ SIGNATURES = {
     "pi_solve_dev": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
     "opi_solve": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
     "opi_solve_dev": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
+    "mdp_server_opts_default": (mdp_server_opts, []),
+    "mdp_server_create": (C.c_int, [C.POINTER(mdp_server_opts), C.POINTER(_h)]),
+    "mdp_server_destroy": (None, [_h]),
+    "mdp_server_submit": (C.c_int, [_h, C.c_int64, C.c_int32, C.c_int32, _vp, _vp, _vp, C.c_double, _vp, _vp, C.POINTER(C.c_int64)]),
+    "mdp_server_poll": (C.c_int, [_h, C.POINTER(C.c_int64), C.POINTER(mdp_stats), C.c_int32, _ip]),
+    "mdp_server_drain": (C.c_int, [_h]),
+    "mdp_server_info": (C.c_int, [_h, _ip, _ip, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "mdp_last_error": (C.c_char_p, []),
     "mdp_version": (C.c_char_p, []),
 }

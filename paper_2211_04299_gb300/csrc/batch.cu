@@ -241,7 +241,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_loop_kernel(BatchDev B,
   for (int j = threadIdx.x; j < B.n; j += blockDim.x) {
     BatchInst& I = B.insts[j];
     if (I.phase == BP_INNER && I.ctl->mode == GM_DONE) I.phase = BP_SWEEPV;
-    if (I.phase != BP_DONE) a += 1;
+    if (I.phase != BP_DONE && I.phase != BP_FREE) a += 1;
   }
   if (a) atomicAdd(&active, a);
   __syncthreads();
@@ -253,6 +253,22 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_loop_kernel(BatchDev B,
     if (active > 0 && !more) B.ctr[2] = 1;
     B.ctr[3] = more ? 1 : 0;
     if (with_cond) cudaGraphSetConditional(hc, more ? 1u : 0u);
+  }
+}
+
+__global__ void __launch_bounds__(CTRL_THREADS) batch_relist_kernel(BatchDev B) {
+  if (threadIdx.x == 0) B.ctr[1] = 0;
+  build_sweep_lists(B);
+}
+
+__global__ void batch_output_one_kernel(const BatchInst* rec, int64_t S, double* vo, int32_t* po) {
+  const float2* tv = rec->tv;
+  const int32_t* pi = rec->pib[rec->cur];
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x) {
+    const float2 x = tv[s];
+    vo[s] = (double)x.x + (double)x.y;
+    po[s] = pi[s];
   }
 }
 
@@ -339,22 +355,6 @@ namespace {
     if (r_ != MDP_OK) return r_ == MDP_EDEVICE ? set_error(r_, #x) : r_;              \
   } while (0)
 
-// Virtual blocks per kernel family: a sweep block streams about 512 KB of P, a matvec block
-// about 256 KB, a Krylov block 4096 rows, an element-wise block 8192 rows.  Each virtual
-// block ends with a block-wide reduction, so larger blocks amortise it; the batch supplies
-// the parallelism that small instances lack.
-void batch_geometry(const DevMDP& d, BatchInst& I) {
-  const int64_t S = d.S;
-  const int64_t row_b = (int64_t)d.kp * 8;
-  auto clampb = [](int64_t x) { return (int)std::max<int64_t>(1, std::min<int64_t>(x, MAX_RED_BLOCKS)); };
-  const int64_t st_sw = std::max<int64_t>(8, 524288 / std::max<int64_t>(1, row_b * d.A));
-  const int64_t st_mv = std::max<int64_t>(32, 262144 / std::max<int64_t>(1, row_b));
-  I.nb_sw = clampb((S + st_sw - 1) / st_sw);
-  I.nb_mv = clampb((S + st_mv - 1) / st_mv);
-  I.nb_ts = clampb((S + 4095) / 4096);
-  I.nb_ew = clampb((S + 8191) / 8192);
-}
-
 void free_batch(mdp_batch_s* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   void* dp[] = {b->pool, b->outpool, b->d_insts, b->d_lists, b->d_ctr, b->d_outp};
@@ -421,20 +421,8 @@ int enqueue_init(mdp_batch_s* b, cudaStream_t st) {
 }
 
 int enqueue_iteration(mdp_batch_s* b, cudaStream_t st, cudaGraphConditionalHandle hc, int with_cond) {
-  const BatchDev& B = b->B;
-  const int maxm = b->o.restart + 1;
-  int r = launch_batch_sweep(B, b->grid_sw, st);
-  if (r != MDP_OK) return r;
-  batch_ctrl_kernel<<<1, CTRL_THREADS, 0, st>>>(B);
-  batch_prologue_kernel<<<b->grid_ew, EW_THREADS, 0, st>>>(B);
-  r = launch_batch_matvec(B, 0, b->grid_mv, st);
-  if (r == MDP_OK) r = launch_batch_cgs(B, maxm, b->grid_ts, st);
-  if (r == MDP_OK) r = launch_batch_estimate(B, maxm, b->grid_ts, st);
-  if (r == MDP_OK) r = launch_batch_matvec(B, 1, b->grid_mv, st);
-  if (r != MDP_OK) return r;
-  batch_value_update_kernel<<<b->grid_ew, EW_THREADS, 0, st>>>(B);
-  batch_loop_kernel<<<1, CTRL_THREADS, 0, st>>>(B, hc, with_cond);
-  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+  const BatchGrids g{b->grid_sw, b->grid_mv, b->grid_ts, b->grid_ew};
+  return batch_enqueue_iteration(b->B, g, b->o.restart + 1, st, hc, with_cond);
 }
 
 int enqueue_output(mdp_batch_s* b, cudaStream_t st) {
@@ -543,7 +531,7 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   BCK(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
   b->stream = b->own;
   const int W = b->o.restart;
-  // workspace layout, instance by instance, 256-byte aligned pieces
+  // workspaces, instance by instance, in one allocation
   b->table.assign(n, BatchInst{});
   std::vector<size_t> off(n);
   size_t tot = 0, otot = 0;
@@ -551,19 +539,8 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   b->po_off.resize(n);
   for (int j = 0; j < n; ++j) {
     const DevMDP& d = *handle_view(hs[j]);
-    BatchInst& I = b->table[j];
-    I.d = d;
-    I.ldq = (d.S + 31) / 32 * 32;
-    I.sqrtS = std::sqrt((double)d.S);
-    batch_geometry(d, I);
-    I.cls_sw = ilog2(ell_sweep_lanes_default(d));
-    I.cls_mv = ilog2(ell_matvec_lanes_default(d));
-    const size_t f = align256((size_t)I.ldq * 4), f2 = align256((size_t)I.ldq * 8);
-    const size_t part = align256(std::max<size_t>((size_t)MAX_RED_BLOCKS * 32,
-                                                  (size_t)I.nb_ts * (WMAX + 1) * 4 + 2 * (size_t)I.nb_mv * 4));
     off[j] = tot;
-    tot += 2 * f2 + 7 * f + align256((size_t)(W + 1) * I.ldq * 4) + 2 * f +
-           align256(sizeof(GmresCtl)) + align256(4 * sizeof(SweepOut)) + part + 256;
+    tot += batch_workspace_bytes(d, W);
     b->vo_off[j] = otot;
     otot += align256((size_t)d.S * 8);
     b->po_off[j] = otot;
@@ -581,28 +558,8 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   }
   b->out_bytes = otot;
   for (int j = 0; j < n; ++j) {
-    BatchInst& I = b->table[j];
-    char* p = b->pool + off[j];
-    const size_t f = align256((size_t)I.ldq * 4), f2 = align256((size_t)I.ldq * 8);
-    auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
-    I.v = (float2*)take(f2);
-    I.tv = (float2*)take(f2);
-    I.phi = (float*)take(f);
-    I.rref = (float*)take(f);
-    I.w0 = (float*)take(f);
-    I.w1 = (float*)take(f);
-    I.rbuf = (float*)take(f);
-    I.d0 = (float*)take(f);
-    I.d1 = (float*)take(f);
-    I.Q = (float*)take((size_t)(W + 1) * I.ldq * 4);
-    I.pib[0] = (int32_t*)take(f);
-    I.pib[1] = (int32_t*)take(f);
-    I.ctl = (GmresCtl*)take(sizeof(GmresCtl));
-    I.sout = (SweepOut*)take(4 * sizeof(SweepOut));
-    I.partials = take(std::max<size_t>((size_t)MAX_RED_BLOCKS * 32,
-                                       (size_t)I.nb_ts * (WMAX + 1) * 4 + 2 * (size_t)I.nb_mv * 4));
-    I.counter = (unsigned*)take(256);
-    I.phase = BP_DONE;
+    batch_setup_inst(*handle_view(hs[j]), W, b->pool + off[j], b->table[j]);
+    b->table[j].phase = BP_DONE;
   }
   // device tables
   BCK(cudaMalloc((void**)&b->d_insts, sizeof(BatchInst) * n));
@@ -877,3 +834,115 @@ int ipi_solve_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, double* co
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ shared with the server
+namespace mdp {
+
+// Virtual blocks per kernel family: a sweep block streams about 512 KB of P, a matvec block
+// about 256 KB, a Krylov block 4096 rows, an element-wise block 8192 rows.  Each virtual
+// block ends with a block-wide reduction, so larger blocks amortise it; the batch supplies
+// the parallelism that small instances lack.
+static void batch_geometry(const DevMDP& d, BatchInst& I) {
+  const int64_t S = d.S;
+  const int64_t row_b = (int64_t)d.kp * 8;
+  auto clampb = [](int64_t x) { return (int)std::max<int64_t>(1, std::min<int64_t>(x, MAX_RED_BLOCKS)); };
+  const int64_t st_sw = std::max<int64_t>(8, 524288 / std::max<int64_t>(1, row_b * d.A));
+  const int64_t st_mv = std::max<int64_t>(32, 262144 / std::max<int64_t>(1, row_b));
+  I.nb_sw = clampb((S + st_sw - 1) / st_sw);
+  I.nb_mv = clampb((S + st_mv - 1) / st_mv);
+  I.nb_ts = clampb((S + 4095) / 4096);
+  I.nb_ew = clampb((S + 8191) / 8192);
+}
+
+static size_t partial_bytes(const BatchInst& I) {
+  return std::max<size_t>((size_t)MAX_RED_BLOCKS * 32,
+                          (size_t)I.nb_ts * (WMAX + 1) * 4 + 2 * (size_t)I.nb_mv * 4);
+}
+
+size_t batch_workspace_bytes(const DevMDP& d, int W) {
+  BatchInst I{};
+  I.d = d;
+  I.ldq = (d.S + 31) / 32 * 32;
+  batch_geometry(d, I);
+  const size_t f = align256((size_t)I.ldq * 4), f2 = align256((size_t)I.ldq * 8);
+  return 2 * f2 + 7 * f + align256((size_t)(W + 1) * I.ldq * 4) + 2 * f +
+         align256(sizeof(GmresCtl)) + align256(4 * sizeof(SweepOut)) + align256(partial_bytes(I)) +
+         256;
+}
+
+void batch_setup_inst(const DevMDP& d, int W, char* base, BatchInst& I) {
+  I = BatchInst{};
+  I.d = d;
+  I.ldq = (d.S + 31) / 32 * 32;
+  I.sqrtS = std::sqrt((double)d.S);
+  batch_geometry(d, I);
+  I.cls_sw = ilog2(ell_sweep_lanes_default(d));
+  I.cls_mv = ilog2(ell_matvec_lanes_default(d));
+  char* p = base;
+  auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
+  const size_t f = (size_t)I.ldq * 4, f2 = (size_t)I.ldq * 8;
+  I.v = (float2*)take(f2);
+  I.tv = (float2*)take(f2);
+  I.phi = (float*)take(f);
+  I.rref = (float*)take(f);
+  I.w0 = (float*)take(f);
+  I.w1 = (float*)take(f);
+  I.rbuf = (float*)take(f);
+  I.d0 = (float*)take(f);
+  I.d1 = (float*)take(f);
+  I.Q = (float*)take((size_t)(W + 1) * I.ldq * 4);
+  I.pib[0] = (int32_t*)take(f);
+  I.pib[1] = (int32_t*)take(f);
+  I.ctl = (GmresCtl*)take(sizeof(GmresCtl));
+  I.sout = (SweepOut*)take(4 * sizeof(SweepOut));
+  I.partials = take(partial_bytes(I));
+  I.counter = (unsigned*)take(256);
+  batch_reset_state(I);
+}
+
+void batch_reset_state(BatchInst& I) {
+  I.phase = BP_SWEEP0;
+  I.cur = 0;
+  I.k = 0;
+  I.reps = 0;
+  I.status = MDP_ENOCONV;
+  I.starting = 0;
+  I.rhs_sel = 0;
+  I.inner = I.restarts = I.checks = I.sweeps = I.loops = 0;
+  I.thr = 0.0;
+  I.res = 0.0;
+}
+
+int batch_enqueue_iteration(const BatchDev& B, const BatchGrids& g, int maxm, cudaStream_t st,
+                            cudaGraphConditionalHandle hc, int with_cond) {
+  int r = launch_batch_sweep(B, g.sw, st);
+  if (r != MDP_OK) return r;
+  batch_ctrl_kernel<<<1, CTRL_THREADS, 0, st>>>(B);
+  batch_prologue_kernel<<<g.ew, EW_THREADS, 0, st>>>(B);
+  r = launch_batch_matvec(B, 0, g.mv, st);
+  if (r == MDP_OK) r = launch_batch_cgs(B, maxm, g.ts, st);
+  if (r == MDP_OK) r = launch_batch_estimate(B, maxm, g.ts, st);
+  if (r == MDP_OK) r = launch_batch_matvec(B, 1, g.mv, st);
+  if (r != MDP_OK) return r;
+  batch_value_update_kernel<<<g.ew, EW_THREADS, 0, st>>>(B);
+  batch_loop_kernel<<<1, CTRL_THREADS, 0, st>>>(B, hc, with_cond);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+int batch_enqueue_relist(const BatchDev& B, cudaStream_t st) {
+  batch_relist_kernel<<<1, CTRL_THREADS, 0, st>>>(B);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+int batch_enqueue_output_one(const BatchInst* rec, int64_t S, double* vo, int32_t* po,
+                             cudaStream_t st) {
+  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((S + 255) / 256, (int64_t)num_sms() * 4));
+  batch_output_one_kernel<<<grid, 256, 0, st>>>(rec, S, vo, po);
+  return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+}
+
+BatchGrids batch_max_grids(int maxm) {
+  return BatchGrids{batch_sweep_grid(), batch_matvec_grid(), batch_ts_grid(maxm), num_sms() * 8};
+}
+
+}  // namespace mdp

@@ -486,7 +486,7 @@ int launch_check_policy(const int32_t* pi, int64_t S, int32_t A, const uint8_t* 
 // the virtual blocks of a compacted list of instances with a grid-stride loop, and each
 // virtual block runs the same kernel body as a single-instance launch whose grid has that
 // instance's block count, so results do not depend on the batch.
-enum BatchPhase { BP_SWEEP0 = 0, BP_INNER = 1, BP_SWEEPV = 2, BP_DONE = 3 };
+enum BatchPhase { BP_SWEEP0 = 0, BP_INNER = 1, BP_SWEEPV = 2, BP_DONE = 3, BP_FREE = 4 };
 constexpr int BATCH_CLASSES = 4;  // ELL lanes per row 1, 2, 4, 8 (class = log2)
 
 struct BatchInst {
@@ -588,6 +588,27 @@ int batch_ts_grid(int maxm);
 int ell_sweep_lanes_default(const DevMDP& d);
 int ell_matvec_lanes_default(const DevMDP& d);
 int krylov_blocks(int64_t S);
+
+// Shared by the batch and the server drivers (batch.cu).
+struct BatchGrids {
+  int sw, mv, ts, ew;  // physical blocks of the sweep, matvec, tall-skinny, element-wise kernels
+};
+// Instance record for data d: geometry, lane classes and the workspace carved from base (a
+// 256-byte aligned block of batch_workspace_bytes(d, W) bytes, zeroed by the caller).
+size_t batch_workspace_bytes(const DevMDP& d, int W);
+void batch_setup_inst(const DevMDP& d, int W, char* base, BatchInst& I);
+// Reset an instance record to the start of a solve (phase SWEEP0, counters zero).
+void batch_reset_state(BatchInst& I);
+// Enqueue one loop iteration (with_cond: end with cudaGraphSetConditional on hc).
+int batch_enqueue_iteration(const BatchDev& B, const BatchGrids& g, int maxm, cudaStream_t st,
+                            cudaGraphConditionalHandle hc, int with_cond);
+// Start of a launch of loop iterations: zero the iteration counter, rebuild the sweep list
+// (instances activated since the last launch join it).
+int batch_enqueue_relist(const BatchDev& B, cudaStream_t st);
+// T(V_K) as double and pi_K of the instance whose record is at rec (device) into vo / po.
+int batch_enqueue_output_one(const BatchInst* rec, int64_t S, double* vo, int32_t* po,
+                             cudaStream_t st);
+BatchGrids batch_max_grids(int maxm);
 
 // Handle access for the batch driver (api.cu): the device view of a handle's data, its
 // device, and the thread-local error message of mdp_last_error.

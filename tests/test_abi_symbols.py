@@ -77,6 +77,23 @@ def test_invalid_arguments_fail_before_any_device_work(built):
     assert lib.mdp_batch_device_bytes(None) == 0
     assert lib.ipi_solve_batch(None, 0, None, None, None, None) == _lib.MDP_EINVAL
     lib.mdp_batch_destroy(None)
+    # servers: option checks precede any device work
+    so = lib.mdp_server_opts_default()
+    assert so.max_slots == 256 and so.iters_per_launch == 4 and so.hbm_budget_bytes == 120 << 30
+    srv = ctypes.c_void_p()
+    for field, bad in (("max_slots", 0), ("iters_per_launch", 0), ("hbm_budget_bytes", 0)):
+        so = lib.mdp_server_opts_default()
+        setattr(so, field, bad)
+        assert lib.mdp_server_create(ctypes.byref(so), ctypes.byref(srv)) == _lib.MDP_EINVAL
+    so = lib.mdp_server_opts_default()
+    so.solver.precision = _lib.MDP_PREC_FP64
+    assert lib.mdp_server_create(ctypes.byref(so), ctypes.byref(srv)) == _lib.MDP_EINVAL
+    assert lib.mdp_server_create(None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_server_submit(None, 1, 1, 1, None, None, None, 0.9, None, None, None) == _lib.MDP_EINVAL
+    assert lib.mdp_server_poll(None, None, None, 0, None) == _lib.MDP_EINVAL
+    assert lib.mdp_server_drain(None) == _lib.MDP_EINVAL
+    assert lib.mdp_server_info(None, None, None, None, None) == _lib.MDP_EINVAL
+    lib.mdp_server_destroy(None)
 
 
 def test_no_cpu_fallback_when_library_missing(tmp_path):
