@@ -633,9 +633,17 @@ def run_serve_bench(args, mg, torch, dist, world, rank, local):
 
         lat64, wall64 = replay(trace, npool, submit64, poll64)
         l64 = np.array([x[0] for x in lat64.values()]) * 1000.0
+        # capacity of the plain path: the same first requests back to back
+        t0 = time.perf_counter()
+        for j in range(sat_n):
+            submit64(j, j % npool)
+        while queue:
+            poll64()
+        sat64 = sat_n / (time.perf_counter() - t0)
         line["fp64_plain"] = {"value": n / wall64, "unit": "solves/s",
                               "latency_ms": {"p50": float(np.percentile(l64, 50)),
                                              "p99": float(np.percentile(l64, 99))},
+                              "capacity": {"value": sat64, "unit": "solves/s", "requests": sat_n},
                               "form": "one request after another: mdp_load_ell + ipi_solve FP64"}
         for h, _ in hs64:
             h.close()
