@@ -177,6 +177,24 @@ class Clocks:
                 "samples": len(sm)}
 
 
+
+# ---------------------------------------------------------------- replicas
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (each rank times its own replica; the job took as long as
+    the slowest).  device: "cuda" under NCCL, "cpu" under gloo."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, seconds_local: float, world: int, device: str = "cuda") -> float:
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return world * units_per_rank / max_over_ranks(seconds_local, world, device)
+
 # ---------------------------------------------------------------- CPU oracle arm
 def oracle_sample(syn_m, counts):
     """Time a bounded sample of the oracle on the workload: one Bellman sweep and one outer
@@ -350,11 +368,8 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     clk = clocks.stop()
     elapsed_ms = ev[0].elapsed_time(ev[-1])
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = world * n * args.steps / (elapsed_ms / 1000.0)
+    value = job_rate(n * args.steps, elapsed_ms / 1000.0, world)
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
     ok = all(code == 0 and all(x["status"] == 0 and x["residual_inf"] <= TOL for x in st)
              for st, code in stats)
     st_last = stats[-1][0]
@@ -428,10 +443,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
             e2e_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * n * e2e_steps / float(tt.item()), "unit": "solves/s",
+        line["e2e"] = {"value": job_rate(n * e2e_steps, dt, world), "unit": "solves/s",
                        "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
                        "steps": e2e_steps}
         del pins
@@ -737,11 +749,8 @@ def main():
     h.set_timing(False)
     elapsed_ms = ev[0].elapsed_time(ev[-1])
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    t = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t.item())
-    value = world * args.steps / (elapsed_ms / 1000.0)
+    value = job_rate(args.steps, elapsed_ms / 1000.0, world)
+    elapsed_ms = max_over_ranks(elapsed_ms, world)
 
     ok = all(s["status"] == 0 and s["residual_inf"] <= TOL for s in stats)
     sweeps = sum(s["timed_sweeps"] for s in stats)
@@ -812,10 +821,7 @@ def main():
             mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        tt = torch.tensor([dt], dtype=torch.float64, device="cuda")
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        line["e2e"] = {"value": world * e2e_steps / float(tt.item()), "unit": "solves/s",
+        line["e2e"] = {"value": job_rate(e2e_steps, dt, world), "unit": "solves/s",
                        "h2d_bytes_per_step": in_bytes,
                        "d2h_bytes_per_step": int(v_h.nbytes + pi_h.nbytes), "steps": e2e_steps}
         del pins
