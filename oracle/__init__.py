@@ -17,6 +17,6 @@ Parity unpinned: none of the functions exported here.
 from .mdp_oracle import (  # noqa: F401
     MDP, q_values, greedy_policy, bellman, policy_matrix, policy_cost, jacobian,
     policy_evaluation, brute_force, value_iteration, policy_iteration,
-    optimistic_policy_iteration, gmres_policy_iteration, policy_eval_gmres,
+    optimistic_policy_iteration, gmres_policy_iteration, policy_eval_gmres, inner_threshold,
     bellman_residual, from_synth,
 )

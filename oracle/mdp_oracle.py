@@ -352,14 +352,29 @@ def policy_eval_gmres(mdp: MDP, pi: np.ndarray, v0=None, target_inf: float = 1e-
                   inner=st.steps, restarts=st.restarts, matvecs=st.matvecs + 2)
 
 
+def inner_threshold(alpha: float, forcing_c: float, phi_inf: float, tol: float) -> float:
+    """Right-hand side of the inexact stopping rule (Sec. 3), alpha_k ||Phi_k||_inf.
+
+    forcing_c = 0: the constant alpha of Alg. 2.  forcing_c > 0: the forcing sequence
+    alpha_k = min(alpha, forcing_c * ||Phi_k||_inf), which lies in [0, alpha] and tends to 0
+    with the residual, so the local convergence theorem of Sec. 3 gives Q-superlinear
+    convergence; the threshold is then kept at or above tol / 10 (reading: an inner solve
+    more accurate than the outer tolerance cannot change the outcome, and below that the
+    arithmetic's floor would stall it)."""
+    if forcing_c > 0.0:
+        return max(min(alpha, forcing_c * phi_inf) * phi_inf, 0.1 * tol)
+    return alpha * phi_inf
+
+
 def gmres_policy_iteration(mdp: MDP, v0=None, alpha: float = 0.1, W: int = 30,
                            tol: float = 1e-8, K: int = 100,
-                           max_inner: int = 100000) -> Result:
+                           max_inner: int = 100000, forcing_c: float = 0.0) -> Result:
     """GMRES(W) Policy Iteration, Alg. 2, step by step.
 
     for k = 0..K-1: pi_k <- GreedyPolicy(V_k); J <- I - gamma P^{pi_k}; V_{k+1} <- V_k;
     Phi_k <- g^{pi_k} - J V_k; (reading: stop here if ||Phi_k||_inf <= tol); run GMRES(W)
-    from V_k while ||g^{pi_k} - J V_{k+1}||_inf > alpha ||Phi_k||_inf.
+    from V_k while ||g^{pi_k} - J V_{k+1}||_inf > alpha_k ||Phi_k||_inf (inner_threshold:
+    alpha_k = alpha unless forcing_c > 0).
     """
     V = np.zeros(mdp.S) if v0 is None else np.array(v0, np.float64)
     res = Result(V, np.zeros(mdp.S, np.int32), np.inf)
@@ -377,8 +392,8 @@ def gmres_policy_iteration(mdp: MDP, v0=None, alpha: float = 0.1, W: int = 30,
             res.margin = b.margin
             return res
         st = _InnerStats()
-        V = _gmres_inner(J, g_pi, V, Phi_k, alpha * phi_inf, W,
-                         max_inner, st)
+        V = _gmres_inner(J, g_pi, V, Phi_k, inner_threshold(alpha, forcing_c, phi_inf, tol),
+                         W, max_inner, st)
         res.inner += st.steps
         res.restarts += st.restarts
         res.matvecs += st.matvecs + 1

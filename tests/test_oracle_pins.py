@@ -343,6 +343,45 @@ def test_igmres_pi_stopping_rule_and_linear_rate():
     assert ratios and max(ratios) <= rate * 1.05
 
 
+def test_adaptive_forcing_is_superlinear():
+    """Theorem (local contraction, Sec. 3.2): a forcing sequence with alpha_k -> 0 gives
+    Q-superlinear convergence, a constant alpha only Q-linear.  On the same MDP as the linear
+    rate test: the constant-alpha residual ratios stay at the linear rate, the adaptive ones
+    (alpha_k = min(alpha, ||Phi_k||_inf)) fall toward 0, and both reach V*."""
+    gamma = 0.8
+    alpha = 0.5 * (1 - gamma) / (1 + gamma)
+    m = oracle.from_synth(mdp_synth.tiny_random(60, 4, seed=71, gamma=gamma, kind="ell", k=6))
+    vstar = oracle.policy_iteration(m, tol=1e-14).v
+    lin = oracle.gmres_policy_iteration(m, alpha=alpha, W=30, tol=1e-13)
+    sup = oracle.gmres_policy_iteration(m, alpha=alpha, W=30, tol=1e-13, forcing_c=1.0)
+    assert lin.status == "ok" and sup.status == "ok"
+    r_lin = [lin.history[i + 1] / lin.history[i] for i in range(2, len(lin.history) - 1)]
+    # ratios of steps that end well above the arithmetic's floor (the last step of a solve
+    # to 1e-13 is limited by FP64 rounding, not by the forcing sequence)
+    r_sup = [sup.history[i + 1] / sup.history[i] for i in range(2, len(sup.history) - 1)
+             if sup.history[i + 1] >= 1e-12]
+    rate = (1 + gamma) / (1 - gamma) * alpha
+    assert max(r_lin) <= rate and min(r_lin) > 1e-2            # linear: bounded away from 0
+    assert len(r_sup) >= 2 and all(b < a for a, b in zip(r_sup, r_sup[1:]))  # ratios shrink
+    assert r_sup[-1] < 1e-3
+    assert sup.outer < lin.outer
+    for r in (lin, sup):
+        np.testing.assert_allclose(r.v, vstar, rtol=0, atol=1e-11 * max(1.0, np.abs(vstar).max()))
+
+
+def test_forcing_sequence_stays_in_range_and_vanishes():
+    """alpha_k lies in [0, alpha] (the theorem's hypothesis) and alpha_k -> 0 as ||Phi_k||
+    -> 0; the threshold never drops below tol / 10."""
+    alpha, tol = 0.05, 1e-8
+    for phi in (10.0, 1.0, 1e-2, 1e-4, 1e-6, 1e-9):
+        thr = oracle.inner_threshold(alpha, 1.0, phi, tol)
+        assert thr <= max(alpha * phi, 0.1 * tol) * (1 + 1e-15)
+        assert thr >= 0.1 * tol
+        assert oracle.inner_threshold(alpha, 0.0, phi, tol) == alpha * phi
+    small = [oracle.inner_threshold(alpha, 1.0, phi, 0.0) / phi for phi in (1e-2, 1e-4, 1e-6)]
+    assert small == sorted(small, reverse=True) and small[-1] <= 1e-6
+
+
 @pytest.mark.parametrize("gamma", [0.9, 0.99])
 def test_igmres_pi_agrees_with_pi_on_config_shaped_input(gamma):
     syn = mdp_synth.ell_uniform(300, 4, 8, gamma, seed=5)

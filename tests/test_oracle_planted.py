@@ -64,3 +64,16 @@ def test_policy_matrix_with_wrong_row_index_is_caught(monkeypatch):
         return orig(mdp, np.roll(np.asarray(pi), 1))
     monkeypatch.setattr(mo, "policy_matrix", bad)
     _fails(pins.test_golden_examples, os.path.join(pins.GOLDEN, "three_state_reset.json"), "igmres")
+
+
+def test_forcing_sequence_that_ignores_the_residual_is_caught(monkeypatch):
+    # alpha_k held at alpha whatever forcing_c says: convergence stays linear
+    monkeypatch.setattr(mo, "inner_threshold", lambda alpha, c, phi, tol: alpha * phi)
+    _fails(pins.test_adaptive_forcing_is_superlinear)
+
+
+def test_forcing_sequence_with_max_instead_of_min_is_caught(monkeypatch):
+    monkeypatch.setattr(mo, "inner_threshold",
+                        lambda alpha, c, phi, tol: max(max(alpha, c * phi) * phi, 0.1 * tol)
+                        if c > 0 else alpha * phi)
+    _fails(pins.test_adaptive_forcing_is_superlinear)
