@@ -61,6 +61,9 @@ def parse():
                          "4 = a batch of 256 independent ELL MDPs solved together, "
                          "5 = a Poisson stream of requests served with continuous batching")
     ap.add_argument("--batch", type=int, default=256, help="instances of the batched workload")
+    ap.add_argument("--forcing-c", type=float, default=0.0,
+                    help="forcing sequence alpha_k = min(alpha, c ||Phi_k||_inf) for the timed "
+                         "solves (0 = constant alpha, Alg. 2)")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workload: keep the library's lanes per row (no autotuning), "
                          "so the launch sequence is the same on every run (for profilers)")
@@ -336,7 +339,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     # launches on (torch's default stream is the legacy stream, handle 0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
+    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=args.forcing_c,
                 flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0)
     b = mg.MDPBatch(hs, o)
     b.set_stream(stream)
@@ -417,6 +420,29 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    line["config"]["forcing_c"] = args.forcing_c
+
+    if args.forcing_c == 0.0:
+        # the same batch with the adaptive forcing sequence (Sec. 3: alpha_k -> 0)
+        ba = mg.MDPBatch(hs, mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
+                                     forcing_c=1.0))
+        ba.set_stream(stream)
+        if not args.no_tune:
+            ba.tune()
+        ba.solve(vd, pd)
+        na = min(args.steps, 5)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(na):
+            _, _, sta, ca = ba.solve(vd, pd)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        line["adaptive_forcing"] = {"forcing_c": 1.0,
+                                    "value": n * na / (a0.elapsed_time(a1) / 1000.0),
+                                    "unit": "solves/s", "converged": ca == 0,
+                                    "outer_max": max(x["outer"] for x in sta),
+                                    "inner_sum": int(sum(x["inner"] for x in sta))}
+        ba.close()
 
     if not args.no_e2e:
         # through the host-pointer API: upload every instance's P and g from pinned memory,
@@ -717,7 +743,7 @@ def main():
     stream = torch.cuda.Stream()  # not the legacy default stream: see run_batch_bench
     torch.cuda.set_stream(stream)
     h.set_stream(stream)
-    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
+    o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=args.forcing_c,
                 flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0)
     v_out = torch.empty(S, dtype=torch.float64, device="cuda")
     pi_out = torch.empty(S, dtype=torch.int32, device="cuda")
@@ -796,6 +822,22 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
+    line["config"]["forcing_c"] = args.forcing_c
+
+    # the same solves with the adaptive forcing sequence (Sec. 3: alpha_k -> 0), for reference
+    if args.forcing_c == 0.0:
+        oa = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=1.0)
+        mg.ipi_solve(h, oa, v_out=v_out, pi_out=pi_out)
+        na = min(args.steps, 10)
+        a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(na):
+            _, _, sta = mg.ipi_solve(h, oa, v_out=v_out, pi_out=pi_out)
+        a1.record(stream)
+        torch.cuda.synchronize()
+        line["adaptive_forcing"] = {"forcing_c": 1.0, "value": na / (a0.elapsed_time(a1) / 1000.0),
+                                    "unit": "solves/s", "outer": sta["outer"], "inner": sta["inner"],
+                                    "converged": sta["status"] == 0}
 
     # end to end through the host-pointer API: upload P, g from pinned memory, solve, copy back
     if not args.no_e2e:

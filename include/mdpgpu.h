@@ -111,6 +111,10 @@ typedef struct {
   int32_t pi_inner_tol_exp; /* PI: relative GMRES tolerance 10^-x for "exact" evaluation */
   int32_t flags;       /* MDP_FLAG_* bits */
   const double* v0;    /* initial V_0 (host for host calls, device for *_dev); NULL = 0 */
+  double forcing_c;    /* forcing sequence of the inner stopping rule (Sec. 3): 0 = constant
+                        * alpha (Alg. 2); c > 0: alpha_k = min(alpha, c ||Phi_k||_inf), which
+                        * tends to 0 (locally Q-superlinear, Sec. 3 theorem), with the inner
+                        * threshold alpha_k ||Phi_k||_inf kept >= tol / 10 */
 } mdp_opts;
 
 /* ipi_solve runs each inner GMRES solve as one CUDA-graph launch with a device-side loop.
@@ -119,7 +123,7 @@ typedef struct {
 #define MDP_FLAG_HOST_LOOP 1
 
 /* alpha 0.1, tol 1e-8, restart 30, max_outer 100, max_inner 3000, precision MIXED,
- * opi_W 50, pi_inner_tol_exp 13, flags 0, v0 NULL. */
+ * opi_W 50, pi_inner_tol_exp 13, flags 0, v0 NULL, forcing_c 0. */
 mdp_opts mdp_opts_default(void);
 
 typedef struct {

@@ -88,6 +88,8 @@ struct mdp_s {
   int grid_sweep = 0;    // blocks per launch (0 = library choice)
   int grid_matvec = 0;
   int grid_krylov = 0;
+  double forcing_c = 0.0;  // forcing sequence of the current ipi_solve (mdp_opts.forcing_c)
+  double thr_floor = 0.0;  // and its floor on the inner threshold (tol / 10)
   size_t data_bytes = 0;
   Workspace ws;
   // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
@@ -95,7 +97,7 @@ struct mdp_s {
   struct InnerGraph {
     cudaGraphExec_t exec = nullptr;
     int kt = -1, W = 0, steps = 0;
-    double alpha = -1.0;
+    double alpha = -1.0, forcing_c = -1.0, thr_floor = -1.0;
     const void* ws = nullptr;
   } ig[2];
   cudaStream_t cap = nullptr;
@@ -345,7 +347,7 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   CK(cudaMemcpyAsync(w.rbuf, rhs ? rhs : w.phi, (size_t)S * ek, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaMemsetAsync(w.d0, 0, (size_t)S * ek, h->stream));
   RK(launch_gmres_init(B, thr, std::sqrt((double)S), W, max_steps, w.sout + slot, alpha,
-                       h->stream, resume, accept_est));
+                       h->stream, resume, accept_est, h->forcing_c, h->thr_floor));
   h->launches += 1;
   HostCtl hc{};
   RK(read_ctl(h, &hc));
@@ -458,7 +460,7 @@ int build_inner_graph(mdp_t h, int variant, const int32_t* pi_dev, double alpha,
       cudaMemsetAsync(w.d0, 0, (size_t)S * ek, h->cap) != cudaSuccess)
     return fail_graph(fail(MDP_EDEVICE, "graph prologue copy"));
   r = launch_gmres_init(B, 0.0, std::sqrt((double)S), W, max_steps, w.sout + (variant == 0 ? 0 : 2),
-                        alpha, h->cap, variant, 1);
+                        alpha, h->cap, variant, 1, h->forcing_c, h->thr_floor);
   if (r != MDP_OK) return fail_graph(r);
   cudaStreamCaptureStatus cst;
   cudaGraph_t capg = nullptr;
@@ -501,6 +503,8 @@ int build_inner_graph(mdp_t h, int variant, const int32_t* pi_dev, double alpha,
   gg.W = W;
   gg.steps = max_steps;
   gg.alpha = alpha;
+  gg.forcing_c = h->forcing_c;
+  gg.thr_floor = h->thr_floor;
   gg.ws = w.ctl;
   return MDP_OK;
 }
@@ -510,6 +514,7 @@ int launch_inner_graph(mdp_t h, int variant, double alpha, int W, int max_steps)
   Workspace& w = h->ws;
   auto& gg = h->ig[variant];
   if (!gg.exec || gg.kt != w.kt || gg.W != W || gg.steps != max_steps || gg.alpha != alpha ||
+      gg.forcing_c != h->forcing_c || gg.thr_floor != h->thr_floor ||
       gg.ws != w.ctl)
     RK(build_inner_graph(h, variant, w.pi, alpha, W, max_steps));
   CK(cudaGraphLaunch(gg.exec, h->stream));
@@ -525,6 +530,8 @@ int check_opts(mdp_t h, const mdp_opts& o) {
   if (!h) return fail(MDP_EINVAL, "null handle");
   if (o.restart < 1 || o.restart > WMAX) return fail(MDP_EINVAL, "restart must be in 1..64");
   if (!(o.alpha >= 0.0 && o.alpha < 1.0)) return fail(MDP_EINVAL, "alpha must be in [0, 1)");
+  if (!(o.forcing_c >= 0.0 && o.forcing_c < INFINITY))
+    return fail(MDP_EINVAL, "forcing_c must be finite and >= 0");
   if (!(o.tol >= 0.0)) return fail(MDP_EINVAL, "tol must be >= 0");
   if (o.max_outer < 0 || o.max_inner < 1) return fail(MDP_EINVAL, "bad iteration caps");
   if (o.precision != MDP_PREC_FP64 && o.precision != MDP_PREC_MIXED)
@@ -583,6 +590,8 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
   RK(ensure_ws(h, arith, o.restart));
   Workspace& w = h->ws;
   const int64_t S = h->d.S;
+  h->forcing_c = o.forcing_c;
+  h->thr_floor = 0.1 * o.tol;
   RK(load_v(h, o.v0, arith));
   int status = MDP_ENOCONV;
   SweepOut so{};
@@ -592,7 +601,7 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
   while (true) {
     if (so.res_inf <= o.tol) { status = MDP_OK; break; }
     if (k >= o.max_outer) break;
-    const double thr = o.alpha * so.res_inf;
+    const double thr = inexact_threshold(o.alpha, o.forcing_c, so.res_inf, h->thr_floor);
     const bool host_loop = (o.flags & MDP_FLAG_HOST_LOOP) != 0;
     if (host_loop) RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, nullptr, nullptr,
                                   w.phi, 0, 1));
@@ -824,6 +833,7 @@ mdp_opts mdp_opts_default(void) {
   o.pi_inner_tol_exp = 13;
   o.flags = 0;
   o.v0 = nullptr;
+  o.forcing_c = 0.0;
   return o;
 }
 

@@ -136,7 +136,7 @@ __device__ void start_inner(const BatchDev& B, BatchInst& I, int variant) {
   // variant 0: J delta = Phi_k (norms sout[0]), threshold alpha ||Phi_k||_inf;
   // variant 1: resumed on the exact residual (norms sout[2]) with the same threshold
   gmres_init_ctl(I.ctl, 0.0, B.alpha, I.sqrtS, B.W, B.max_steps, I.sout + (variant ? 2 : 0),
-                 variant, 1);
+                 variant, 1, B.forcing_c, B.thr_floor);
 }
 
 // The decisions of the outer loop of Alg. 2 after a sweep, one thread per instance.
@@ -180,7 +180,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_ctrl_kernel(BatchDev B) {
       I.status = MDP_ENOCONV;
       I.phase = BP_DONE;
     } else {
-      I.thr = B.alpha * res;
+      I.thr = inexact_threshold(B.alpha, B.forcing_c, res, B.thr_floor);
       I.k += 1;
       I.reps = 0;
       start_inner(B, I, 0);
@@ -507,6 +507,7 @@ int check_batch_opts(const mdp_opts& o) {
   if (o.restart < 1 || o.restart > WMAX) return set_error(MDP_EINVAL, "restart must be in 1..64");
   if (!(o.alpha > 0.0 && o.alpha < 1.0)) return set_error(MDP_EINVAL, "alpha must be in (0, 1)");
   if (!(o.tol >= 0.0)) return set_error(MDP_EINVAL, "tol must be >= 0");
+  if (!(o.forcing_c >= 0.0 && o.forcing_c < INFINITY)) return set_error(MDP_EINVAL, "forcing_c must be finite and >= 0");
   if (o.max_outer < 0 || o.max_inner < 1) return set_error(MDP_EINVAL, "bad iteration caps");
   if (o.precision != MDP_PREC_MIXED) return set_error(MDP_EINVAL, "a batch runs in MDP_PREC_MIXED");
   if (o.v0) return set_error(MDP_EINVAL, "a batch starts from V_0 = 0 (v0 must be NULL)");
@@ -582,6 +583,8 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   B.n = n;
   B.alpha = b->o.alpha;
   B.tol = b->o.tol;
+  B.forcing_c = b->o.forcing_c;
+  B.thr_floor = 0.1 * b->o.tol;
   B.W = W;
   B.max_steps = b->o.max_inner;
   B.max_outer = b->o.max_outer;

@@ -868,8 +868,9 @@ __device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp)
 }
 
 __global__ void gmres_init_kernel(GmresCtl* c, double thr, double alpha, double sqrtS, int W,
-                                  int max_steps, const SweepOut* rhs, int resume, int accept_est) {
-  gmres_init_ctl(c, thr, alpha, sqrtS, W, max_steps, rhs, resume, accept_est);
+                                  int max_steps, const SweepOut* rhs, int resume, int accept_est,
+                                  double forcing_c, double thr_floor) {
+  gmres_init_ctl(c, thr, alpha, sqrtS, W, max_steps, rhs, resume, accept_est, forcing_c, thr_floor);
 }
 
 __global__ void gmres_loop_cond_kernel(cudaGraphConditionalHandle hc, GmresCtl* c, int cap) {
@@ -1206,9 +1207,9 @@ int launch_batch_estimate(const BatchDev& B, int maxm, int grid, cudaStream_t st
 
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
                       const SweepOut* rhs_norms, double alpha, cudaStream_t st, int resume,
-                      int accept_est) {
+                      int accept_est, double forcing_c, double thr_floor) {
   gmres_init_kernel<<<1, 1, 0, st>>>(B.ctl, thr, alpha, sqrtS, W, max_steps, rhs_norms, resume,
-                                     accept_est);
+                                     accept_est, forcing_c, thr_floor);
   return ok_or_dev();
 }
 

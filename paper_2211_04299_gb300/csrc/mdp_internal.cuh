@@ -325,6 +325,20 @@ struct GmresCtl {
   float xscalef;
 };
 
+// Right-hand side of the inexact stopping rule for outer residual res = ||Phi_k||_inf
+// (Sec. 3): alpha ||Phi_k||_inf with the constant alpha of Alg. 2 (forcing_c = 0), or
+// alpha_k ||Phi_k||_inf with the forcing sequence alpha_k = min(alpha, forcing_c res), kept at
+// or above floor.  Host and device evaluate the same expression.
+__host__ __device__ inline double inexact_threshold(double alpha, double forcing_c, double res,
+                                                    double floor) {
+  if (forcing_c > 0.0) {
+    const double ak = alpha < forcing_c * res ? alpha : forcing_c * res;
+    const double t = ak * res;
+    return t > floor ? t : floor;
+  }
+  return alpha * res;
+}
+
 __device__ __forceinline__ void gmres_set_scale(GmresCtl* c, double s) {
   c->xscale = s;
   c->xscalef = (float)s;
@@ -336,7 +350,8 @@ __device__ __forceinline__ void gmres_set_scale(GmresCtl* c, double s) {
 // once with delta = 0.
 __device__ inline void gmres_init_ctl(GmresCtl* c, double thr, double alpha, double sqrtS, int W,
                                       int max_steps, const SweepOut* rhs, int resume,
-                                      int accept_est) {
+                                      int accept_est, double forcing_c = 0.0,
+                                      double thr_floor = 0.0) {
   c->W = W;
   c->max_steps = max_steps;
   c->sqrtS = sqrtS;
@@ -354,7 +369,7 @@ __device__ inline void gmres_init_ctl(GmresCtl* c, double thr, double alpha, dou
   if (resume) {
     c->thr = c->thr_saved;
   } else {
-    c->thr = alpha > 0.0 ? alpha * rhs->res_inf : thr;
+    c->thr = alpha > 0.0 ? inexact_threshold(alpha, forcing_c, rhs->res_inf, thr_floor) : thr;
     c->thr_saved = c->thr;
   }
   c->accept_est = accept_est;
@@ -458,7 +473,7 @@ int launch_loop_cond(cudaGraphConditionalHandle hc, GmresCtl* ctl, int cap, cuda
 // exact test to the caller (the next Bellman sweep).
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
                       const SweepOut* rhs_norms, double alpha, cudaStream_t st, int resume = 0,
-                      int accept_est = 0);
+                      int accept_est = 0, double forcing_c = 0.0, double thr_floor = 0.0);
 
 // Value update v += delta (double or double-float), delta = chosen by ctl (or given).
 int launch_value_update(int kt, void* v, const void* d0, const void* d1, const GmresCtl* ctl,
@@ -526,6 +541,7 @@ struct BatchDev {
   BatchInst* insts;
   int n;
   double alpha, tol;
+  double forcing_c, thr_floor;  // forcing sequence of the inner stopping rule
   int W, max_steps, max_outer;
   BatchList sw;                 // sweeps due
   BatchList mv;                 // inner solves running (matvec blocks)

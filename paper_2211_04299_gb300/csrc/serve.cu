@@ -335,6 +335,8 @@ int create_server(const mdp_server_opts* opts, mdp_server_s* s) {
   if (so.restart < 1 || so.restart > WMAX) return set_error(MDP_EINVAL, "restart must be in 1..64");
   if (!(so.alpha > 0.0 && so.alpha < 1.0)) return set_error(MDP_EINVAL, "alpha must be in (0, 1)");
   if (!(so.tol >= 0.0)) return set_error(MDP_EINVAL, "tol must be >= 0");
+  if (!(so.forcing_c >= 0.0 && so.forcing_c < INFINITY))
+    return set_error(MDP_EINVAL, "forcing_c must be finite and >= 0");
   if (so.max_outer < 0 || so.max_inner < 1) return set_error(MDP_EINVAL, "bad iteration caps");
   if (so.precision != MDP_PREC_MIXED) return set_error(MDP_EINVAL, "the server runs in MDP_PREC_MIXED");
   if (so.v0) return set_error(MDP_EINVAL, "requests start from V_0 = 0 (v0 must be NULL)");
@@ -374,6 +376,8 @@ int create_server(const mdp_server_opts* opts, mdp_server_s* s) {
   B.n = n;
   B.alpha = so.alpha;
   B.tol = so.tol;
+  B.forcing_c = so.forcing_c;
+  B.thr_floor = 0.1 * so.tol;
   B.W = so.restart;
   B.max_steps = so.max_inner;
   B.max_outer = so.max_outer;

@@ -43,6 +43,7 @@ def test_ctypes_table_matches_header(built):
     assert lib.mdp_version().decode().startswith("mdpgpu")
     o = lib.mdp_opts_default()
     assert o.restart == 30 and abs(o.alpha - 0.1) < 1e-15 and o.precision == 1
+    assert o.forcing_c == 0.0 and not o.v0
 
 
 def test_invalid_arguments_fail_before_any_device_work(built):
@@ -68,6 +69,10 @@ def test_invalid_arguments_fail_before_any_device_work(built):
     o = lib.mdp_opts_default()
     o.restart = 0
     assert lib.mdp_batch_create(one, 1, ctypes.byref(o), ctypes.byref(b)) == _lib.MDP_EINVAL
+    o = lib.mdp_opts_default()
+    o.forcing_c = -1.0
+    assert lib.mdp_batch_create(one, 1, ctypes.byref(o), ctypes.byref(b)) == _lib.MDP_EINVAL
+    assert b"forcing_c" in lib.mdp_last_error()
     assert not b.value
     assert lib.mdp_batch_solve(None, None, None, None) == _lib.MDP_EINVAL
     assert lib.mdp_batch_solve_dev(None, None, None, None) == _lib.MDP_EINVAL
