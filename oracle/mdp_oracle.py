@@ -366,6 +366,49 @@ def inner_threshold(alpha: float, forcing_c: float, phi_inf: float, tol: float) 
     return alpha * phi_inf
 
 
+def inexact_pi_vi(mdp: MDP, v0=None, alpha: float = 0.1, tol: float = 1e-8, K: int = 100,
+                  max_inner: int = 100000, forcing_c: float = 0.0) -> Result:
+    """Inexact Policy Iteration (Alg. 1) with VI as the inner solver (Sec. 3: OPI whose number
+    of inner steps is set by the stopping rule).
+
+    for k = 0..K-1: pi_k <- GreedyPolicy(V_k); Phi_k = g^{pi_k} - J^{pi_k} V_k (= T V_k - V_k);
+    (reading: stop if ||Phi_k||_inf <= tol); W <- V_k; repeat W <- T^{pi_k} W = g^{pi_k} +
+    gamma P^{pi_k} W while ||g^{pi_k} - J^{pi_k} W||_inf > alpha_k ||Phi_k||_inf; V_{k+1} <- W.
+    The first inner step is taken unconditionally (the residual at V_k is Phi_k itself).
+    """
+    V = np.zeros(mdp.S) if v0 is None else np.array(v0, np.float64)
+    res = Result(V, np.zeros(mdp.S, np.int32), np.inf)
+    for k in range(K):
+        b = bellman(mdp, V)                     # pi_k <- GreedyPolicy(V_k), T V_k
+        res.sweeps += 1
+        pi_k = b.pi
+        phi_inf = b.res_inf                     # ||g^{pi_k} - J^{pi_k} V_k||_inf
+        res.history.append(phi_inf)
+        if phi_inf <= tol:
+            res.v, res.pi, res.residual, res.outer = b.Tv, pi_k, phi_inf, k
+            res.margin = b.margin
+            return res
+        thr = inner_threshold(alpha, forcing_c, phi_inf, tol)
+        g_pi = policy_cost(mdp, pi_k)
+        P_pi = policy_matrix(mdp, pi_k)
+        W = b.Tv                                # first step: T^{pi_k} V_k = T V_k
+        steps = 1
+        while steps < max_inner:
+            TW = g_pi + mdp.gamma * (P_pi @ W)  # T^{pi_k} W
+            res.matvecs += 1
+            if float(np.max(np.abs(TW - W))) <= thr:
+                break
+            W = TW
+            steps += 1
+        res.inner += steps
+        V = W
+    b = bellman(mdp, V)
+    res.sweeps += 1
+    res.v, res.pi, res.residual, res.outer, res.status = b.Tv, b.pi, b.res_inf, K, "noconv"
+    res.margin = b.margin
+    return res
+
+
 def gmres_policy_iteration(mdp: MDP, v0=None, alpha: float = 0.1, W: int = 30,
                            tol: float = 1e-8, K: int = 100,
                            max_inner: int = 100000, forcing_c: float = 0.0) -> Result:

@@ -382,6 +382,27 @@ def test_forcing_sequence_stays_in_range_and_vanishes():
     assert small == sorted(small, reverse=True) and small[-1] <= 1e-6
 
 
+@pytest.mark.parametrize("gamma", [0.9, 0.95])
+def test_inexact_pi_with_vi_inner_reduces_to_pi_and_vi(gamma):
+    """Alg. 1 with VI as the inner solver.  alpha -> 0: every evaluation is exact, so the outer
+    iteration is PI's (same policies, same count).  alpha = (1+gamma)/2 > gamma: one
+    application of T^{pi_k} already contracts the residual by gamma (T^{pi_k} V_k = T V_k), so
+    each outer step takes exactly one inner step and the iterates are VI's, bit for bit."""
+    m = oracle.from_synth(mdp_synth.tiny_random(80, 4, seed=3, gamma=gamma, kind="ell", k=6))
+    pi_r = oracle.policy_iteration(m, tol=1e-12)
+    exact = oracle.inexact_pi_vi(m, alpha=1e-14, tol=1e-12)
+    assert exact.status == "ok" and exact.outer == pi_r.outer
+    assert np.array_equal(exact.pi, pi_r.pi)
+    np.testing.assert_allclose(exact.v, pi_r.v, rtol=0, atol=1e-10)
+    vi_r = oracle.value_iteration(m, tol=1e-10)
+    one = oracle.inexact_pi_vi(m, alpha=(1 + gamma) / 2, tol=1e-10, K=10000)
+    assert one.inner == one.outer == vi_r.outer
+    assert one.history == vi_r.history and np.array_equal(one.v, vi_r.v)
+    mid = oracle.inexact_pi_vi(m, alpha=0.1, tol=1e-10)
+    assert mid.status == "ok" and vi_r.outer > mid.outer > pi_r.outer
+    assert np.max(np.abs(mid.v - pi_r.v)) <= gamma * 1e-10 / (1 - gamma) * 1.01
+
+
 @pytest.mark.parametrize("gamma", [0.9, 0.99])
 def test_igmres_pi_agrees_with_pi_on_config_shaped_input(gamma):
     syn = mdp_synth.ell_uniform(300, 4, 8, gamma, seed=5)

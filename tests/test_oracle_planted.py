@@ -77,3 +77,15 @@ def test_forcing_sequence_with_max_instead_of_min_is_caught(monkeypatch):
                         lambda alpha, c, phi, tol: max(max(alpha, c * phi) * phi, 0.1 * tol)
                         if c > 0 else alpha * phi)
     _fails(pins.test_adaptive_forcing_is_superlinear)
+
+
+def test_policy_rows_of_the_wrong_action_are_caught(monkeypatch):
+    # every other P^pi built for an evaluation uses the next action's rows
+    orig = mo.policy_matrix
+
+    def drifting(mdp, pi):
+        drifting.calls += 1
+        return orig(mdp, pi) if drifting.calls % 2 else orig(mdp, (pi + 1) % mdp.A)
+    drifting.calls = 0
+    monkeypatch.setattr(mo, "policy_matrix", drifting)
+    _fails(pins.test_inexact_pi_with_vi_inner_reduces_to_pi_and_vi, 0.9)
