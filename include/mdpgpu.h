@@ -242,6 +242,14 @@ int opi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
 int opi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
                   mdp_stats* stats);
 
+/* Inexact policy iteration with VI as the inner solver (Alg. 1; Sec. 3 notes it is OPI whose
+ * number of inner steps is set by the stopping rule): per outer step, V <- T^{pi_k} V from
+ * T V_k while ||g^{pi_k} - J^{pi_k} V||_inf > alpha_k ||Phi_k||_inf (alpha_k as in ipi_solve,
+ * at most max_inner steps).  stats.inner counts the applications of T^{pi_k}. */
+int ipi_vi_solve(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out, mdp_stats* stats);
+int ipi_vi_solve_dev(mdp_t h, const mdp_opts* opts, double* v_out, int32_t* pi_out,
+                     mdp_stats* stats);
+
 /* ---------------------------------------------------------------------------- batches */
 /* A batch solves n independent MDPs with iGMRES-PI (Alg. 2, mixed precision) in one
  * CUDA-graph launch: each instance runs the outer loop as a device-side state machine, and

@@ -17,7 +17,7 @@ from ._lib import (MDP_F32, MDP_F64, MDP_FLAG_HOST_LOOP, MDP_PREC_FP64,  # noqa:
 
 __all__ = [
     "MDPHandle", "mdp_create_dense", "mdp_create_ell", "bellman_apply", "policy_eval_gmres",
-    "ipi_solve", "vi_solve", "pi_solve", "opi_solve", "opts", "MDP_PREC_FP64",
+    "ipi_solve", "vi_solve", "pi_solve", "opi_solve", "ipi_vi_solve", "opts", "MDP_PREC_FP64",
     "MDPBatch", "ipi_solve_batch", "MDPServer",
     "MDP_PREC_MIXED", "MDPError", "lib",
 ]
@@ -223,6 +223,11 @@ def pi_solve(h, o=None, device=False, v_out=None, pi_out=None):
 
 def opi_solve(h, o=None, device=False, v_out=None, pi_out=None):
     return _solve("opi_solve", h, o, device, v_out, pi_out)
+
+
+def ipi_vi_solve(h, o=None, device=False, v_out=None, pi_out=None):
+    """Inexact PI with VI as the inner solver (Alg. 1) -> (v, pi, stats)."""
+    return _solve("ipi_vi_solve", h, o, device, v_out, pi_out)
 
 
 def from_synth(m, device: bool = False) -> MDPHandle:

@@ -87,6 +87,8 @@ SIGNATURES = {
     "pi_solve_dev": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
     "opi_solve": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
     "opi_solve_dev": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
+    "ipi_vi_solve": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
+    "ipi_vi_solve_dev": (C.c_int, [_h, C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
     "mdp_server_opts_default": (mdp_server_opts, []),
     "mdp_server_create": (C.c_int, [C.POINTER(mdp_server_opts), C.POINTER(_h)]),
     "mdp_server_destroy": (None, [_h]),

@@ -547,7 +547,7 @@ double now_s() {
 }
 
 // ---------------------------------------------------------------- solvers (device buffers)
-enum Method { METH_IPI = 0, METH_VI = 1, METH_PI = 2, METH_OPI = 3 };
+enum Method { METH_IPI = 0, METH_VI = 1, METH_PI = 2, METH_OPI = 3, METH_IPI_VI = 4 };
 
 // Policy evaluation to an absolute target by repeated inner solves on the current residual
 // (one solve in FP64; in FP32 Krylov each solve cuts the residual by up to 1e-5 and the
@@ -674,6 +674,22 @@ int run_solver(mdp_t h, int method, const mdp_opts& o, double* v_out, int32_t* p
         RK(sweep(h, arith, w.v, w.pi, nullptr, w.tv, nullptr, nullptr, nullptr, w.sout + 2, &st));
         std::swap(w.v, w.tv);
       }
+    } else if (method == METH_IPI_VI) {
+      // Alg. 1 with VI as the inner solver: V <- T^{pi_k} V while the residual of pi_k,
+      // ||g^{pi_k} - J^{pi_k} V||_inf = ||T^{pi_k} V - V||_inf, is above alpha_k ||Phi_k||_inf.
+      // The first step is T V_k of the greedy sweep; each further policy sweep gives the
+      // residual at the current V and T^{pi_k} V together.
+      const double thr = inexact_threshold(o.alpha, o.forcing_c, so.res_inf, 0.1 * o.tol);
+      std::swap(w.v, w.tv);
+      int j = 1;
+      for (; j < o.max_inner; ++j) {
+        RK(sweep(h, arith, w.v, w.pi, nullptr, w.tv, nullptr, nullptr, nullptr, w.sout + 2, &st));
+        SweepOut sr{};
+        RK(read_sout(h, 2, &sr));
+        if (!(sr.res_inf > thr)) break;
+        std::swap(w.v, w.tv);
+      }
+      st.inner += j;
     } else {  // PI: evaluate pi_k "exactly" (relative 10^-x of ||Phi_k||)
       const double target = so.res_inf * std::pow(10.0, -(double)o.pi_inner_tol_exp);
       double r = 0;
@@ -1045,5 +1061,6 @@ SOLVER(ipi_solve, METH_IPI)
 SOLVER(vi_solve, METH_VI)
 SOLVER(pi_solve, METH_PI)
 SOLVER(opi_solve, METH_OPI)
+SOLVER(ipi_vi_solve, METH_IPI_VI)
 
 }  // extern "C"

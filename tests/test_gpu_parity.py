@@ -179,7 +179,7 @@ def test_policy_eval_gmres_parity(mg, kind, prec, W):
 
 
 # ------------------------------------------------------------------ solvers
-SOLVER_NAMES = ["ipi_solve", "vi_solve", "pi_solve", "opi_solve"]
+SOLVER_NAMES = ["ipi_solve", "vi_solve", "pi_solve", "opi_solve", "ipi_vi_solve"]
 
 
 @pytest.mark.parametrize("name", SOLVER_NAMES)
@@ -197,6 +197,35 @@ def test_small_solvers_match_brute_force_scale_oracle(mg, name, kind, prec):
     assert st["status"] == 0, st
     assert st["residual_inf"] <= tol
     assert rel_err(v, ref.v) <= (1e-10 if prec == "fp64" else 1e-9)
+    check_policy(pi, oracle.bellman(m, ref.v))
+
+
+def test_ipi_vi_limits_match_pi_and_vi(mg):
+    """Inexact PI with VI inner steps (Alg. 1): alpha -> 0 evaluates exactly (PI's outer count
+    and policy); alpha = (1+gamma)/2 takes one inner step per outer step (VI's count)."""
+    syn = make("ell", 200, 4, 6, seed=8, gamma=0.9)
+    m = oracle.from_synth(syn)
+    h = mg.from_synth(syn)
+    pi_r = oracle.policy_iteration(m, tol=1e-12)
+    v, pi, st = mg.ipi_vi_solve(h, mg.opts(tol=1e-12, precision="fp64", alpha=1e-14,
+                                           max_inner=5000))
+    assert st["status"] == 0 and st["outer"] == pi_r.outer
+    check_policy(pi, oracle.bellman(m, pi_r.v))
+    _, _, st_vi = mg.vi_solve(h, mg.opts(tol=1e-10, precision="fp64", max_outer=5000))
+    _, _, st1 = mg.ipi_vi_solve(h, mg.opts(tol=1e-10, precision="fp64", alpha=0.95,
+                                           max_outer=5000))
+    assert st1["status"] == 0 and st1["inner"] == st1["outer"] == st_vi["outer"]
+
+
+def test_ipi_vi_config1_fp64_matches_oracle(mg):
+    syn = mdp_synth.config(1)
+    m = oracle.from_synth(syn)
+    ref = oracle.inexact_pi_vi(m, alpha=0.1, tol=1e-13)
+    h = mg.from_synth(syn)
+    tol = 1e-10 * np.max(np.abs(ref.v)) * (1 - 0.95) / (2 * 0.95)
+    v, pi, st = mg.ipi_vi_solve(h, mg.opts(tol=tol, precision="fp64", alpha=0.1))
+    assert st["status"] == 0 and st["residual_inf"] <= tol
+    assert rel_err(v, ref.v) <= 1e-10
     check_policy(pi, oracle.bellman(m, ref.v))
 
 
