@@ -445,30 +445,42 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
         ba.close()
 
     if not args.no_e2e:
-        # through the host-pointer API: upload every instance's P and g from pinned memory,
-        # solve the batch, copy every v and pi back
-        pins = [(torch.from_numpy(np.ascontiguousarray(syn.col)).pin_memory(),
-                 torch.from_numpy(np.ascontiguousarray(syn.val)).pin_memory(),
-                 np.ascontiguousarray(syn.g)) for syn in syns]
-        in_bytes = int(sum(c.numel() * 4 + v.numel() * 4 + g.nbytes for c, v, g in pins))
+        # through the host-pointer API: every step uploads every instance's P and g from pinned
+        # memory (mdp_load_ell_async), solves the batch and copies every v and pi back.  Two
+        # sets of handles and batches alternate, so step i+1's uploads run while step i solves.
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+        pins = [(pin(syn.col), pin(syn.val), pin(syn.g)) for syn in syns]
+        in_bytes = int(sum(c.nbytes + v.nbytes + g.nbytes for c, v, g in pins))
         vh = [np.empty(syn.S) for syn in syns]
         ph = [np.empty(syn.S, np.int32) for syn in syns]
         out_bytes = int(sum(x.nbytes for x in vh) + sum(x.nbytes for x in ph))
+        hs2 = [mg.from_synth(syn) for syn in syns]
+        b2 = mg.MDPBatch(hs2, o)
+        b2.set_stream(stream)
+        if not args.no_tune:
+            b2.tune()
+        sets = [(hs, b), (hs2, b2)]
 
-        def e2e_step():
-            for h, (c, v, g) in zip(hs, pins):
-                mg.mdp_load_ell(h, c.numpy(), v.numpy(), g)
-            b.solve(vh, ph)
+        def e2e_run(k):
+            for hh, (c, v, g) in zip(sets[0][0], pins):
+                mg.mdp_load_ell_async(hh, c, v, g)
+            for i in range(k):
+                if i + 1 < k:
+                    for hh, (c, v, g) in zip(sets[(i + 1) % 2][0], pins):
+                        mg.mdp_load_ell_async(hh, c, v, g)
+                sets[i % 2][1].solve(vh, ph)
 
-        e2e_step()
+        e2e_run(2)
         torch.cuda.synchronize()
         barrier()
-        e2e_steps = min(args.steps, 3)
+        e2e_steps = min(args.steps, 4)
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            e2e_step()
+        e2e_run(e2e_steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        b2.close()
+        for hh in hs2:
+            hh.close()
         line["e2e"] = {"value": job_rate(n * e2e_steps, dt, world), "unit": "solves/s",
                        "h2d_bytes_per_step": in_bytes, "d2h_bytes_per_step": out_bytes,
                        "steps": e2e_steps}
@@ -839,30 +851,40 @@ def main():
                                     "unit": "solves/s", "outer": sta["outer"], "inner": sta["inner"],
                                     "converged": sta["status"] == 0}
 
-    # end to end through the host-pointer API: upload P, g from pinned memory, solve, copy back
+    # end to end through the host-pointer API: every step uploads P and g from pinned host
+    # memory (mdp_load_*_async), solves, and copies v and pi back to host arrays.  Two handles
+    # alternate, so step i+1's upload runs while step i solves.
     if not args.no_e2e:
-        g_np = np.ascontiguousarray(syn.g)
+        g_np = torch.from_numpy(np.ascontiguousarray(syn.g)).pin_memory().numpy()
+        h2 = mg.from_synth(syn)
+        hs_e2e = [h, h2]
         if syn.kind == "dense":
             pins = [torch.from_numpy(syn.P).pin_memory()]
-            load = lambda: mg.mdp_load_dense(h, pins[0].numpy(), g_np)
+            load = lambda hh: mg.mdp_load_dense_async(hh, pins[0].numpy(), g_np)
         else:
             pins = [torch.from_numpy(np.ascontiguousarray(syn.col)).pin_memory(),
                     torch.from_numpy(np.ascontiguousarray(syn.val)).pin_memory()]
-            load = lambda: mg.mdp_load_ell(h, pins[0].numpy(), pins[1].numpy(), g_np)
+            load = lambda hh: mg.mdp_load_ell_async(hh, pins[0].numpy(), pins[1].numpy(), g_np)
         in_bytes = sum(int(t.numel() * t.element_size()) for t in pins) + g_np.nbytes
         v_h = np.empty(S)
         pi_h = np.empty(S, np.int32)
-        e2e_steps = min(args.steps, 5)
-        load()
-        mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
+        e2e_steps = min(args.steps, 8)
+
+        def e2e_run(k):
+            load(hs_e2e[0])
+            for i in range(k):
+                if i + 1 < k:
+                    load(hs_e2e[(i + 1) % 2])
+                mg.ipi_solve(hs_e2e[i % 2], o, v_out=v_h, pi_out=pi_h)
+
+        e2e_run(2)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            load()
-            mg.ipi_solve(h, o, v_out=v_h, pi_out=pi_h)
+        e2e_run(e2e_steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        h2.close()
         line["e2e"] = {"value": job_rate(e2e_steps, dt, world), "unit": "solves/s",
                        "h2d_bytes_per_step": in_bytes,
                        "d2h_bytes_per_step": int(v_h.nbytes + pi_h.nbytes), "steps": e2e_steps}

@@ -84,6 +84,15 @@ int mdp_create_ell_dev(int64_t S, int32_t A, int32_t k, const int32_t* col, cons
  * upload path of a client that reuses one handle for a stream of same-shaped MDPs. */
 int mdp_load_dense(mdp_t h, const void* P, const double* g);
 int mdp_load_ell(mdp_t h, const int32_t* col, const void* val, const double* g);
+/* The same loads, enqueued on the handle's stream without waiting: the copies (asynchronous
+ * from pinned host memory), the layout change and the device validation run in stream order,
+ * and the host arrays must stay valid until the next call on this handle returns.  That next
+ * call (a solve, bellman_apply, policy_eval_gmres, another load, mdp_set_stream, a batch over
+ * the handle) first waits for this handle's stream and returns the validation result
+ * (MDP_EINVAL for invalid data, nothing else done).  With two handles a client uploads the
+ * next MDP while the current one solves. */
+int mdp_load_dense_async(mdp_t h, const void* P, const double* g);
+int mdp_load_ell_async(mdp_t h, const int32_t* col, const void* val, const double* g);
 
 void mdp_destroy(mdp_t h);
 

@@ -135,6 +135,16 @@ def mdp_load_ell(h: MDPHandle, col, val, g) -> None:
     _check(lib().mdp_load_ell(h.ptr, _ptr(col), _ptr(val), _ptr(g)), "mdp_load_ell")
 
 
+def mdp_load_dense_async(h: MDPHandle, P, g) -> None:
+    """Enqueue the load (arrays must stay alive until the next call on h returns)."""
+    _check(lib().mdp_load_dense_async(h.ptr, _ptr(P), _ptr(g)), "mdp_load_dense_async")
+
+
+def mdp_load_ell_async(h: MDPHandle, col, val, g) -> None:
+    """Enqueue the load (arrays must stay alive until the next call on h returns)."""
+    _check(lib().mdp_load_ell_async(h.ptr, _ptr(col), _ptr(val), _ptr(g)), "mdp_load_ell_async")
+
+
 def opts(**kw) -> mdp_opts:
     """mdp_opts with the library defaults, overridden by keyword (v0 must stay alive)."""
     o = lib().mdp_opts_default()

@@ -56,6 +56,8 @@ SIGNATURES = {
     "mdp_create_ell_dev": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),
     "mdp_load_dense": (C.c_int, [_h, _vp, _vp]),
     "mdp_load_ell": (C.c_int, [_h, _vp, _vp, _vp]),
+    "mdp_load_dense_async": (C.c_int, [_h, _vp, _vp]),
+    "mdp_load_ell_async": (C.c_int, [_h, _vp, _vp, _vp]),
     "mdp_destroy": (None, [_h]),
     "mdp_set_stream": (C.c_int, [_h, _vp]),
     "mdp_info": (C.c_int, [_h, C.POINTER(C.c_int64), _ip, _ip, _ip, _ip, _dp]),

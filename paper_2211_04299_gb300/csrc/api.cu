@@ -79,6 +79,9 @@ struct mdp_s {
   float2* gdf = nullptr;
   uint8_t* mask = nullptr;
   double* gstage = nullptr;
+  int* vflags = nullptr;   // validation flags of mdp_create / mdp_load
+  int* h_vflags = nullptr; // pinned copy of them
+  int vpending = 0;        // an enqueued load not yet checked (mdp_load_*_async)
   cudaStream_t stream = nullptr;
   cudaStream_t own = nullptr;
   int device = 0;
@@ -724,12 +727,18 @@ int validate_args(int64_t S, int32_t A, int32_t k, int kind, int dt, double gamm
   return MDP_OK;
 }
 
-int upload_data(mdp_t h, const void* P, const int32_t* col, const double* g, const uint8_t* mask) {
+// Enqueue the upload of P (and columns), g and the mask on the handle's stream, the cost
+// layout change and the device validation, whose flags are copied to pinned host memory.
+int enqueue_upload(mdp_t h, const void* P, const int32_t* col, const double* g,
+                   const uint8_t* mask) {
   DevMDP& d = h->d;
   const size_t eb = d.pdt == MDP_F32 ? 4 : 8;
   cudaStream_t s = h->stream;
   if (d.kind == KIND_DENSE) {
-    CK(cudaMemsetAsync(h->P, 0, (size_t)d.S * d.A * d.ld * eb, s));
+    // zero only the pad columns S..ld-1 of every row; the copies below write the rest
+    if (d.ld > d.S)
+      CK(cudaMemset2DAsync((char*)h->P + (size_t)d.S * eb, (size_t)d.ld * eb, 0,
+                           (size_t)(d.ld - d.S) * eb, (size_t)d.S * d.A, s));
     for (int a = 0; a < d.A; ++a) {
       const char* src = (const char*)P + (size_t)a * d.S * d.S * eb;
       char* dst = (char*)h->P + (size_t)a * d.ld * eb;
@@ -737,8 +746,12 @@ int upload_data(mdp_t h, const void* P, const int32_t* col, const double* g, con
                            (size_t)d.S, cudaMemcpyDefault, s));
     }
   } else {
-    CK(cudaMemsetAsync(h->P, 0, (size_t)d.S * d.A * d.kp * eb, s));
-    CK(cudaMemsetAsync(h->col, 0, (size_t)d.S * d.A * d.kp * 4, s));
+    if (d.kp > d.k) {  // pad entries k..kp-1 of every row: value 0, column 0
+      CK(cudaMemset2DAsync((char*)h->P + (size_t)d.k * eb, (size_t)d.kp * eb, 0,
+                           (size_t)(d.kp - d.k) * eb, (size_t)d.S * d.A, s));
+      CK(cudaMemset2DAsync((char*)h->col + (size_t)d.k * 4, (size_t)d.kp * 4, 0,
+                           (size_t)(d.kp - d.k) * 4, (size_t)d.S * d.A, s));
+    }
     for (int a = 0; a < d.A; ++a) {
       const char* src = (const char*)P + (size_t)a * d.S * d.k * eb;
       char* dst = (char*)h->P + (size_t)a * d.kp * eb;
@@ -754,15 +767,21 @@ int upload_data(mdp_t h, const void* P, const int32_t* col, const double* g, con
   RK(launch_cost_transpose(h->gstage, h->g64, h->gdf, d.S, d.A, s));
   if (mask) CK(cudaMemcpyAsync(h->mask, mask, (size_t)d.S * d.A, cudaMemcpyDefault, s));
   // validate on the device
-  int* flags = nullptr;
-  CK(cudaMalloc((void**)&flags, 8 * sizeof(int)));
-  cudaMemsetAsync(flags, 0, 8 * sizeof(int), s);
-  int r = launch_validate(d, flags, s);
-  int hf[8] = {0};
-  cudaMemcpyAsync(hf, flags, sizeof(hf), cudaMemcpyDeviceToHost, s);
-  cudaError_t e = cudaStreamSynchronize(s);
-  cudaFree(flags);
-  if (r != MDP_OK || e != cudaSuccess) return fail(MDP_EDEVICE, std::string("validation: ") + cudaGetErrorString(e));
+  int* flags = h->vflags;  // allocated with the handle (a per-load cudaFree would stall the device)
+  CK(cudaMemsetAsync(flags, 0, 8 * sizeof(int), s));
+  RK(launch_validate(d, flags, s));
+  CK(cudaMemcpyAsync(h->h_vflags, flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  h->vpending = 1;
+  return MDP_OK;
+}
+
+// Wait for an enqueued upload (this handle's stream only) and report its validation.
+int finish_upload(mdp_t h) {
+  if (!h->vpending) return MDP_OK;
+  h->vpending = 0;
+  const cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (e != cudaSuccess) return fail(MDP_EDEVICE, std::string("upload: ") + cudaGetErrorString(e));
+  const int* hf = h->h_vflags;
   if (hf[0]) return fail(MDP_EINVAL, "transition probabilities must be finite and >= 0");
   if (hf[1]) return fail(MDP_EINVAL, "ELL column index out of range [0, S)");
   if (hf[2]) return fail(MDP_EINVAL, "a transition row does not sum to 1 within tolerance");
@@ -812,6 +831,9 @@ int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int 
   if (r == MDP_OK) r = alloc0((void**)&h->g64, (size_t)S * A * 8, acc);
   if (r == MDP_OK && dt == MDP_F32) r = alloc0((void**)&h->gdf, (size_t)S * A * 8, acc);
   if (r == MDP_OK) r = alloc0((void**)&h->gstage, (size_t)S * A * 8, acc);
+  if (r == MDP_OK) r = alloc0((void**)&h->vflags, 8 * sizeof(int), acc);
+  if (r == MDP_OK && cudaMallocHost((void**)&h->h_vflags, 8 * sizeof(int)) != cudaSuccess)
+    r = fail(MDP_ENOMEM, "cudaMallocHost of the validation flags failed");
   if (r == MDP_OK && mask) r = alloc0((void**)&h->mask, (size_t)S * A, acc);
   if (r != MDP_OK) return bail(r);
   h->data_bytes = acc;
@@ -820,7 +842,8 @@ int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int 
   d.g64 = h->g64;
   d.gdf = h->gdf;
   d.mask = h->mask;
-  r = upload_data(h, P, col, g, mask);
+  r = enqueue_upload(h, P, col, g, mask);
+  if (r == MDP_OK) r = finish_upload(h);
   if (r != MDP_OK) return bail(r);
   *out = h;
   return MDP_OK;
@@ -831,6 +854,7 @@ int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int 
 // ====================================================================== C ABI
 namespace mdp {
 const DevMDP* handle_view(mdp_t h) { return h ? &h->d : nullptr; }
+int handle_finish_pending(mdp_t h) { return h ? finish_upload(h) : MDP_OK; }
 int handle_device(mdp_t h) { return h ? h->device : -1; }
 int set_error(int code, const char* msg) { return fail(code, msg); }
 }  // namespace mdp
@@ -875,24 +899,35 @@ int mdp_create_ell_dev(int64_t S, int32_t A, int32_t k, const int32_t* col, cons
   return create_common(S, A, k, KIND_ELL, val, val_dtype, col, g, gamma, mask, out);
 }
 
-int mdp_load_dense(mdp_t h, const void* P, const double* g) {
+int mdp_load_dense_async(mdp_t h, const void* P, const double* g) {
   g_err.clear();
   if (!h || h->d.kind != KIND_DENSE || !P || !g) return fail(MDP_EINVAL, "bad handle or input");
-  return upload_data(h, P, nullptr, g, nullptr);
+  RK(finish_upload(h));
+  return enqueue_upload(h, P, nullptr, g, nullptr);
 }
-int mdp_load_ell(mdp_t h, const int32_t* col, const void* val, const double* g) {
+int mdp_load_ell_async(mdp_t h, const int32_t* col, const void* val, const double* g) {
   g_err.clear();
   if (!h || h->d.kind != KIND_ELL || !col || !val || !g) return fail(MDP_EINVAL, "bad handle or input");
-  return upload_data(h, val, col, g, nullptr);
+  RK(finish_upload(h));
+  return enqueue_upload(h, val, col, g, nullptr);
+}
+int mdp_load_dense(mdp_t h, const void* P, const double* g) {
+  RK(mdp_load_dense_async(h, P, g));
+  return finish_upload(h);
+}
+int mdp_load_ell(mdp_t h, const int32_t* col, const void* val, const double* g) {
+  RK(mdp_load_ell_async(h, col, val, g));
+  return finish_upload(h);
 }
 
 void mdp_destroy(mdp_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_ws(h->ws);
-  void* ptrs[] = {h->P, h->col, h->g64, h->gdf, h->mask, h->gstage};
+  void* ptrs[] = {h->P, h->col, h->g64, h->gdf, h->mask, h->gstage, h->vflags};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  if (h->h_vflags) cudaFreeHost(h->h_vflags);
   for (cudaEvent_t e : h->ev) cudaEventDestroy(e);
   for (auto& gg : h->ig)
     if (gg.exec) cudaGraphExecDestroy(gg.exec);
@@ -903,6 +938,7 @@ void mdp_destroy(mdp_t h) {
 
 int mdp_set_stream(mdp_t h, void* stream) {
   if (!h) return fail(MDP_EINVAL, "null handle");
+  RK(finish_upload(h));
   CK(cudaStreamSynchronize(h->stream));
   h->stream = stream ? (cudaStream_t)stream : h->own;
   return MDP_OK;
@@ -964,6 +1000,7 @@ int64_t mdp_device_bytes(mdp_t h) {
 
 int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double* margin,
                       double* res_inf, int32_t precision) {
+  if (h && h->vpending) RK(finish_upload(h));
   g_err.clear();
   if (!h || !v) return fail(MDP_EINVAL, "null handle or v");
   const int arith = precision == MDP_PREC_MIXED ? 1 : 0;
@@ -981,6 +1018,7 @@ int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double*
 
 int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res_inf,
                   int32_t precision) {
+  if (h && h->vpending) RK(finish_upload(h));
   g_err.clear();
   if (!h || !v) return fail(MDP_EINVAL, "null handle or v");
   const int arith = precision == MDP_PREC_MIXED ? 1 : 0;
@@ -1000,6 +1038,7 @@ int bellman_apply(mdp_t h, const double* v, double* Tv, int32_t* pi, double* res
 
 int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double target_inf,
                           const mdp_opts* opts, double* v_out, mdp_stats* stats) {
+  if (h && h->vpending) RK(finish_upload(h));
   g_err.clear();
   mdp_opts o = normalise(opts);
   RK(check_opts(h, o));
@@ -1048,6 +1087,7 @@ int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double targe
     g_err.clear();                                                                      \
     mdp_opts o = normalise(opts);                                                       \
     RK(check_opts(h, o));                                                               \
+    RK(finish_upload(h));                                                               \
     if (!v_out) return fail(MDP_EINVAL, "null v_out");                                  \
     if (method == METH_OPI && o.opi_W < 1) return fail(MDP_EINVAL, "opi_W must be >= 1");  \
     if (method == METH_IPI) return run_ipi(h, o, v_out, pi_out, stats);                 \

@@ -524,6 +524,7 @@ int create_batch(const mdp_t* hs, int32_t n, const mdp_opts* opts, mdp_batch_s* 
   for (int j = 0; j < n; ++j) {
     const DevMDP* d = handle_view(hs[j]);
     if (!d) return set_error(MDP_EINVAL, "null handle in batch");
+    BRK(handle_finish_pending(hs[j]));
     if (d->kind != KIND_ELL || d->pdt != MDP_F32)
       return set_error(MDP_EINVAL, "a batch takes ELL handles with FP32 transition data");
     if (handle_device(hs[j]) != b->device)
@@ -615,6 +616,9 @@ int run_batch(mdp_batch_s* b, double* const* v_out, int32_t* const* pi_out, mdp_
     b->h_outp[j] = device_out ? (void*)v_out[j] : (void*)(b->outpool + b->vo_off[j]);
     b->h_outp[n + j] = device_out ? (void*)pi_out[j] : (void*)(b->outpool + b->po_off[j]);
   }
+  // loads enqueued with mdp_load_*_async on the batch's handles must have landed (and passed
+  // validation) before the batch reads their data
+  for (mdp_t h : b->hs) BRK(handle_finish_pending(h));
   const bool host_loop = (b->o.flags & MDP_FLAG_HOST_LOOP) != 0;
   if (!host_loop && !b->exec) BRK(build_graph(b));
   BCK(cudaMemcpyAsync(b->d_outp, b->h_outp, sizeof(void*) * 2 * n, cudaMemcpyHostToDevice, b->stream));

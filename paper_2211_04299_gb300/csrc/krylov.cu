@@ -929,38 +929,100 @@ __global__ void cost_transpose_kernel(const double* gAS, double* gSA, float2* gd
   }
 }
 
+// Compensated (Kahan) FP32 sum: error about 2 eps |sum| independent of the length, so FP32
+// rows can be checked against the 1e-5 row-sum tolerance at the speed of the FP32 pipes.
+struct KahanF {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float y = __fsub_rn(x, c);
+    const float t = __fadd_rn(s, y);
+    c = __fsub_rn(__fsub_rn(t, s), y);
+    s = t;
+  }
+  __device__ __forceinline__ double value() const { return (double)s - (double)c; }
+};
+
+__device__ __forceinline__ int bad_prob(float x) { return !(x >= 0.f) || isinf(x); }
+__device__ __forceinline__ int bad_prob(double x) { return !(x >= 0.0) || isinf(x); }
+
 // flags: [0] negative / non-finite probability, [1] column out of range, [2] row sum off,
 //        [3] non-finite cost, [4] state without an allowed action
+// Whole padded rows are read with 128-bit loads (pads hold zeros and column 0): a warp per
+// dense row, a thread per ELL row.  FP32 rows are summed with KahanF, FP64 rows in FP64.
 template <class PT>
 __global__ void validate_kernel(DevMDP d, int* flags) {
   const int lane = threadIdx.x & 31;
   const int64_t nrows = d.S * d.A;
-  const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
   const PT* P = (const PT*)d.P;
-  const double tol = 1e-5;  // FP32 rows widened to FP64 keep their ~1e-7 rounding
-  const int64_t rowlen = d.kind == KIND_DENSE ? d.ld : d.kp;
-  const int64_t n = d.kind == KIND_DENSE ? d.S : d.k;
-  for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
-    const PT* row = P + r * rowlen;
-    double sum = 0.0;
-    int badv = 0, badc = 0;
-    for (int64_t j = lane; j < n; j += 32) {
-      const double x = (double)row[j];
-      if (!(x >= 0.0) || isinf(x)) badv = 1;
-      sum += x;
-      if (d.kind == KIND_ELL) {
-        const int32_t cj = d.col[r * rowlen + j];
-        if (cj < 0 || cj >= d.S) badc = 1;
+  const double tol = 1e-5;  // FP32 rows keep their ~1e-7 rounding
+  int badv = 0, badc = 0, bads = 0;
+  if (d.kind == KIND_DENSE) {
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    const int64_t nv = d.ld / 4;
+    for (int64_t r = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
+      const PT* row = P + r * d.ld;
+      double tot;
+      if constexpr (sizeof(PT) == 4) {
+        KahanF k;
+        for (int64_t q = lane; q < nv; q += 32) {
+          const float4 x = __ldcs(reinterpret_cast<const float4*>(row) + q);
+          badv |= bad_prob(x.x) | bad_prob(x.y) | bad_prob(x.z) | bad_prob(x.w);
+          k.add(x.x); k.add(x.y); k.add(x.z); k.add(x.w);
+        }
+        tot = k.value();
+      } else {
+        double sm = 0.0;
+        for (int64_t q = lane; q < nv; q += 32) {
+          const double2 x0 = __ldcs(reinterpret_cast<const double2*>(row) + 2 * q);
+          const double2 x1 = __ldcs(reinterpret_cast<const double2*>(row) + 2 * q + 1);
+          badv |= bad_prob(x0.x) | bad_prob(x0.y) | bad_prob(x1.x) | bad_prob(x1.y);
+          sm += (x0.x + x0.y) + (x1.x + x1.y);
+        }
+        tot = sm;
       }
+      tot = warp_sum(tot);
+      if (lane == 0 && !(fabs(tot - 1.0) <= tol)) bads = 1;
     }
-    sum = warp_sum(sum);
-    badv = __any_sync(0xffffffffu, badv);
-    badc = __any_sync(0xffffffffu, badc);
-    if (lane == 0) {
-      if (badv) atomicOr(flags + 0, 1);
-      if (badc) atomicOr(flags + 1, 1);
-      if (!(fabs(sum - 1.0) <= tol)) atomicOr(flags + 2, 1);
+  } else {
+    const int nv = d.kp / 4;
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+      const PT* row = P + r * d.kp;
+      const int4* cr = reinterpret_cast<const int4*>(d.col + r * d.kp);
+      double tot;
+      if constexpr (sizeof(PT) == 4) {
+        KahanF k;
+        for (int q = 0; q < nv; ++q) {
+          const float4 x = __ldcs(reinterpret_cast<const float4*>(row) + q);
+          badv |= bad_prob(x.x) | bad_prob(x.y) | bad_prob(x.z) | bad_prob(x.w);
+          k.add(x.x); k.add(x.y); k.add(x.z); k.add(x.w);
+        }
+        tot = k.value();
+      } else {
+        double sm = 0.0;
+        for (int q = 0; q < nv; ++q) {
+          const double2 x0 = __ldcs(reinterpret_cast<const double2*>(row) + 2 * q);
+          const double2 x1 = __ldcs(reinterpret_cast<const double2*>(row) + 2 * q + 1);
+          badv |= bad_prob(x0.x) | bad_prob(x0.y) | bad_prob(x1.x) | bad_prob(x1.y);
+          sm += (x0.x + x0.y) + (x1.x + x1.y);
+        }
+        tot = sm;
+      }
+      for (int q = 0; q < nv; ++q) {
+        const int4 c = __ldcs(cr + q);
+        badc |= (c.x < 0 || c.x >= d.S) | (c.y < 0 || c.y >= d.S) | (c.z < 0 || c.z >= d.S) |
+                (c.w < 0 || c.w >= d.S);
+      }
+      if (!(fabs(tot - 1.0) <= tol)) bads = 1;
     }
+  }
+  badv = __any_sync(0xffffffffu, badv);
+  badc = __any_sync(0xffffffffu, badc);
+  bads = __any_sync(0xffffffffu, bads);
+  if (lane == 0) {
+    if (badv) atomicOr(flags + 0, 1);
+    if (badc) atomicOr(flags + 1, 1);
+    if (bads) atomicOr(flags + 2, 1);
   }
   for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nrows;
        t += (int64_t)gridDim.x * blockDim.x)

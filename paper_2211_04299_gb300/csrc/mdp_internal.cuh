@@ -629,6 +629,8 @@ BatchGrids batch_max_grids(int maxm);
 // Handle access for the batch driver (api.cu): the device view of a handle's data, its
 // device, and the thread-local error message of mdp_last_error.
 const DevMDP* handle_view(mdp_t h);
+// Wait for a load enqueued by mdp_load_*_async on the handle (its stream only), check it.
+int handle_finish_pending(mdp_t h);
 int handle_device(mdp_t h);
 int set_error(int code, const char* msg);
 

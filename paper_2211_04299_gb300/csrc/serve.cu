@@ -192,9 +192,9 @@ int start_upload(mdp_server_s* s, Req* r) {
   r->d.mask = nullptr;
   // workspace zero (V_0 = 0, zero pads of the Krylov vectors, reduction counters)
   SCK(cudaMemsetAsync(r->ws, 0, batch_workspace_bytes(d, W), s->us));
-  if (d.kp != d.k) {
-    SCK(cudaMemsetAsync(val, 0, rows * d.kp * 4, s->us));
-    SCK(cudaMemsetAsync(col, 0, rows * d.kp * 4, s->us));
+  if (d.kp != d.k) {  // pad entries k..kp-1 of every row: value 0, column 0
+    SCK(cudaMemset2DAsync(val + d.k, (size_t)d.kp * 4, 0, (size_t)(d.kp - d.k) * 4, rows, s->us));
+    SCK(cudaMemset2DAsync(col + d.k, (size_t)d.kp * 4, 0, (size_t)(d.kp - d.k) * 4, rows, s->us));
   }
   for (int a = 0; a < d.A; ++a) {
     SCK(cudaMemcpy2DAsync(val + (size_t)a * d.kp, (size_t)d.A * d.kp * 4, r->val + (size_t)a * d.S * d.k,

@@ -296,6 +296,52 @@ def test_warm_start_is_resume(mg):
     assert st2["outer"] <= st3["outer"]
 
 
+@pytest.mark.parametrize("kind", ["ell", "dense"])
+def test_async_loads_equal_sync_loads_and_report_invalid_data(mg, kind):
+    """mdp_load_*_async enqueues the upload and validation; the next call on the handle waits
+    for that handle's stream and reports the validation (invalid data -> EINVAL)."""
+    import torch
+    a = make(kind, 300, 4, 7, seed=51, val_dtype=np.float32, gamma=0.95)
+    b = make(kind, 300, 4, 7, seed=52, val_dtype=np.float32, gamma=0.95)
+    o = mg.opts(tol=1e-9, precision="mixed")
+
+    def load(h, syn, asyn):
+        pin = lambda x: torch.from_numpy(np.ascontiguousarray(x)).pin_memory().numpy()
+        g = pin(syn.g)
+        if kind == "dense":
+            P = pin(syn.P)
+            (mg.mdp_load_dense_async if asyn else mg.mdp_load_dense)(h, P, g)
+            return (P, g)
+        col, val = pin(syn.col), pin(syn.val)
+        (mg.mdp_load_ell_async if asyn else mg.mdp_load_ell)(h, col, val, g)
+        return (col, val, g)
+
+    h0, h1 = mg.from_synth(a), mg.from_synth(a)
+    keep = load(h0, b, False)
+    v_ref, pi_ref, _ = mg.ipi_solve(h0, o)
+    keep1 = load(h1, b, True)                  # enqueued ...
+    keep2 = load(h0, a, True)                  # ... and another handle's load meanwhile
+    v1, pi1, _ = mg.ipi_solve(h1, o)          # waits for h1's stream only
+    np.testing.assert_array_equal(v1, v_ref)
+    np.testing.assert_array_equal(pi1, pi_ref)
+    v0, _, st0 = mg.ipi_solve(h0, o)
+    va, _, _ = mg.ipi_solve(mg.from_synth(a), o)
+    np.testing.assert_array_equal(v0, va)
+    bad = make(kind, 300, 4, 7, seed=53, val_dtype=np.float32, gamma=0.95)
+    if kind == "dense":
+        bad.P = bad.P.copy(); bad.P[0, 0, :] *= 2.0
+    else:
+        bad.val = bad.val.copy(); bad.val[0, 0, :] *= 2.0
+    keep3 = load(h1, bad, True)
+    with pytest.raises(mg.MDPError) as e:
+        mg.ipi_solve(h1, o)
+    assert e.value.code == -1
+    keep4 = load(h1, b, True)                  # the handle recovers with valid data
+    v2, _, st2 = mg.ipi_solve(h1, o)
+    np.testing.assert_array_equal(v2, v_ref)
+    del keep, keep1, keep2, keep3, keep4
+
+
 def test_iteration_cap_reports_noconv(mg):
     syn = make("ell", 200, 3, 4, seed=6, gamma=0.99)
     h = mg.from_synth(syn)
