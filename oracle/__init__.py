@@ -18,6 +18,6 @@ from .mdp_oracle import (  # noqa: F401
     MDP, q_values, greedy_policy, bellman, policy_matrix, policy_cost, jacobian,
     policy_evaluation, brute_force, value_iteration, policy_iteration,
     optimistic_policy_iteration, gmres_policy_iteration, policy_eval_gmres, inner_threshold,
-    inexact_pi_vi,
+    inexact_pi_vi, two_level,
     bellman_residual, from_synth,
 )

@@ -285,11 +285,36 @@ class _InnerStats:
     breakdown: bool = False
 
 
+def two_level(mdp: MDP, pi: np.ndarray, block: int):
+    """Two-level preconditioner for J^pi = I - gamma P^pi (a preconditioned inner solver, the
+    direction the paper names as future work in Sec. 5).  States are aggregated into consecutive
+    blocks of `block` (the last one shorter); R averages a vector over each block, Pr copies a
+    block value to its states (R Pr = I), and the coarse operator is the Galerkin product
+    J_c = R J^pi Pr.  Returns (R, Pr, J_c, minv) with minv(q) = q + Pr J_c^{-1} R q."""
+    J = jacobian(mdp, pi)
+    S = mdp.S
+    agg = np.arange(S) // block
+    nc = int(agg[-1]) + 1
+    Pr = sp.csr_matrix((np.ones(S), (np.arange(S), agg)), shape=(S, nc))
+    sizes = np.bincount(agg, minlength=nc).astype(np.float64)
+    R = sp.diags(1.0 / sizes) @ Pr.T.tocsr()
+    JPr = J @ Pr
+    Jc = np.asarray((R @ JPr).todense() if sp.issparse(JPr) else R @ JPr)
+    lu = sla.lu_factor(Jc)
+
+    def minv(q):
+        return q + Pr @ sla.lu_solve(lu, R @ q)
+    return R, Pr, Jc, minv
+
+
 def _gmres_inner(J, g_pi: np.ndarray, V_k: np.ndarray, Phi_k: np.ndarray, threshold: float,
-                 W: int, max_steps: int, st: _InnerStats) -> np.ndarray:
+                 W: int, max_steps: int, st: _InnerStats, minv=None) -> np.ndarray:
     """The inner loop of Alg. 2 (GMRES(W) on J^pi V = g^pi started at V_k), run while
     ||g^pi - J^pi V_{k+1}||_inf > threshold.  Arnoldi with modified Gram-Schmidt; the true
-    residual is formed at every test, as the while-condition of Alg. 2 states."""
+    residual is formed at every test, as the while-condition of Alg. 2 states.  With minv
+    (a preconditioner M^{-1}) the Arnoldi process runs on J M^{-1} (right preconditioning) and
+    the iterate is base + M^{-1} Q y, so residuals keep their meaning."""
+    mv = (lambda x: x) if minv is None else minv
     n = V_k.shape[0]
     V_next = V_k.copy()                       # V_{k+1} <- V_k
     x0 = V_k.copy()                           # base of the current cycle (reading)
@@ -305,7 +330,7 @@ def _gmres_inner(J, g_pi: np.ndarray, V_k: np.ndarray, Phi_k: np.ndarray, thresh
         st.matvecs += 1
         if not (np.max(np.abs(r_true)) > threshold) or st.steps >= max_steps:
             return V_next
-        q = J @ Q[:, i - 1]                   # q <- J^pi [Q]_i
+        q = J @ mv(Q[:, i - 1])               # q <- J^pi [Q]_i  (J^pi M^{-1} [Q]_i)
         st.matvecs += 1
         qnorm0 = float(np.linalg.norm(q))
         for j in range(1, i + 1):             # modified Gram-Schmidt
@@ -316,10 +341,10 @@ def _gmres_inner(J, g_pi: np.ndarray, V_k: np.ndarray, Phi_k: np.ndarray, thresh
         if H[i, i - 1] <= BREAKDOWN_REL * qnorm0:   # ||q||_2 = 0: lucky breakdown
             y = _lsq(H[: i + 1, :i], beta)
             st.breakdown = True
-            return Q[:, :i] @ y + x0
+            return mv(Q[:, :i] @ y) + x0
         Q[:, i] = q / H[i, i - 1]             # [Q]_{i+1} <- q / [H]_{i+1,i}
         y = _lsq(H[: i + 1, :i], beta)        # y~ <- argmin || ||Phi||_2 e_1 - H y ||_2
-        V_next = Q[:, :i] @ y + x0            # V_{k+1} <- Q y~ + base
+        V_next = mv(Q[:, :i] @ y) + x0        # V_{k+1} <- Q y~ + base  (M^{-1} Q y~)
         if i == W:                            # restart
             x0 = V_next.copy()
             r = g_pi - J @ V_next
@@ -337,7 +362,7 @@ def _gmres_inner(J, g_pi: np.ndarray, V_k: np.ndarray, Phi_k: np.ndarray, thresh
 
 
 def policy_eval_gmres(mdp: MDP, pi: np.ndarray, v0=None, target_inf: float = 1e-10,
-                      W: int = 30, max_steps: int = 100000) -> Result:
+                      W: int = 30, max_steps: int = 100000, precond_block: int = 0) -> Result:
     """Inexact policy evaluation alone: GMRES(W) on (I - gamma P^pi) V = g^pi started at v0
     until ||g^pi - (I - gamma P^pi) V||_inf <= target_inf (Alg. 2's inner loop with an
     absolute threshold)."""
@@ -346,7 +371,8 @@ def policy_eval_gmres(mdp: MDP, pi: np.ndarray, v0=None, target_inf: float = 1e-
     g_pi = policy_cost(mdp, pi)
     Phi = g_pi - J @ V0
     st = _InnerStats()
-    V = _gmres_inner(J, g_pi, V0, Phi, target_inf, W, max_steps, st)
+    minv = two_level(mdp, pi, precond_block)[3] if precond_block > 0 else None
+    V = _gmres_inner(J, g_pi, V0, Phi, target_inf, W, max_steps, st, minv)
     res = float(np.max(np.abs(g_pi - J @ V))) if mdp.S else 0.0
     return Result(V, np.asarray(pi, np.int32), res, "ok" if res <= target_inf else "noconv",
                   inner=st.steps, restarts=st.restarts, matvecs=st.matvecs + 2)
@@ -411,7 +437,8 @@ def inexact_pi_vi(mdp: MDP, v0=None, alpha: float = 0.1, tol: float = 1e-8, K: i
 
 def gmres_policy_iteration(mdp: MDP, v0=None, alpha: float = 0.1, W: int = 30,
                            tol: float = 1e-8, K: int = 100,
-                           max_inner: int = 100000, forcing_c: float = 0.0) -> Result:
+                           max_inner: int = 100000, forcing_c: float = 0.0,
+                           precond_block: int = 0) -> Result:
     """GMRES(W) Policy Iteration, Alg. 2, step by step.
 
     for k = 0..K-1: pi_k <- GreedyPolicy(V_k); J <- I - gamma P^{pi_k}; V_{k+1} <- V_k;
@@ -435,8 +462,9 @@ def gmres_policy_iteration(mdp: MDP, v0=None, alpha: float = 0.1, W: int = 30,
             res.margin = b.margin
             return res
         st = _InnerStats()
+        minv = two_level(mdp, pi_k, precond_block)[3] if precond_block > 0 else None
         V = _gmres_inner(J, g_pi, V, Phi_k, inner_threshold(alpha, forcing_c, phi_inf, tol),
-                         W, max_inner, st)
+                         W, max_inner, st, minv)
         res.inner += st.steps
         res.restarts += st.restarts
         res.matvecs += st.matvecs + 1

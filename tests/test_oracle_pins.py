@@ -403,6 +403,58 @@ def test_inexact_pi_with_vi_inner_reduces_to_pi_and_vi(gamma):
     assert np.max(np.abs(mid.v - pi_r.v)) <= gamma * 1e-10 / (1 - gamma) * 1.01
 
 
+def test_two_level_coarse_operator_is_the_galerkin_product():
+    """J_c[I][J] = (1/|I|) sum_{s in I} sum_{s' in J} J[s][s'] for consecutive blocks (the last
+    one shorter), R Pr = I, and J_c = I - gamma P_c with P_c >= 0 row-stochastic."""
+    syn = mdp_synth.tiny_random(37, 3, seed=12, gamma=0.9)
+    m = oracle.from_synth(syn)
+    pi = oracle.bellman(m, np.zeros(37)).pi
+    R, Pr, Jc, _ = oracle.two_level(m, pi, 8)
+    J = np.asarray(oracle.jacobian(m, pi))
+    blocks = [list(range(i, min(i + 8, 37))) for i in range(0, 37, 8)]
+    ref = np.array([[sum(J[s, t] for s in bi for t in bj) / len(bi) for bj in blocks]
+                    for bi in blocks])
+    np.testing.assert_allclose(Jc, ref, rtol=0, atol=1e-14)
+    np.testing.assert_allclose((R @ Pr).toarray(), np.eye(len(blocks)), rtol=0, atol=1e-15)
+    Pc = (np.eye(len(blocks)) - Jc) / 0.9
+    assert np.all(Pc >= -1e-15)
+    np.testing.assert_allclose(Pc.sum(axis=1), 1.0, rtol=0, atol=1e-13)
+
+
+def test_preconditioned_gmres_unrestarted_is_exact():
+    """Right-preconditioned GMRES without restarts (W >= n) solves J V = g^pi exactly within n
+    steps, like plain GMRES (the preconditioner is nonsingular)."""
+    syn = mdp_synth.tiny_random(30, 3, seed=13, gamma=0.95, kind="ell", k=5)
+    m = oracle.from_synth(syn)
+    pi = oracle.bellman(m, np.zeros(30)).pi
+    exact = oracle.policy_evaluation(m, pi)
+    r = oracle.policy_eval_gmres(m, pi, target_inf=1e-12, W=40, precond_block=4)
+    assert r.status == "ok" and r.inner <= 30
+    np.testing.assert_allclose(r.v, exact, rtol=0, atol=1e-10 * np.abs(exact).max())
+
+
+def test_two_level_preconditioner_cuts_inner_steps():
+    """Banded transitions with gamma = 0.999 (the growth-model shape): the slow modes of
+    I - gamma P^pi are smooth over the state index, which the coarse correction removes; the
+    preconditioned evaluation needs a tenth of the plain GMRES(30) steps or fewer."""
+    syn = mdp_synth.ell_banded(20000, 4, 16, 512, 64, 0.999, seed=7, val_dtype=np.float32)
+    m = oracle.from_synth(syn)
+    pi = oracle.bellman(m, np.zeros(20000)).pi
+    plain = oracle.policy_eval_gmres(m, pi, target_inf=1e-6, W=30)
+    pre = oracle.policy_eval_gmres(m, pi, target_inf=1e-6, W=30, precond_block=128)
+    assert plain.status == "ok" and pre.status == "ok"
+    assert pre.inner * 10 <= plain.inner
+
+
+def test_preconditioned_igmres_pi_matches_pi():
+    syn = mdp_synth.ell_banded(3000, 16, 32, 512, 64, 0.999, seed=1003, val_dtype=np.float32)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-12)
+    r = oracle.gmres_policy_iteration(m, alpha=0.1, W=30, tol=1e-10, precond_block=64)
+    assert r.status == "ok"
+    np.testing.assert_allclose(r.v, ref.v, rtol=0, atol=1e-10 * np.abs(ref.v).max() / (1 - 0.999))
+
+
 @pytest.mark.parametrize("gamma", [0.9, 0.99])
 def test_igmres_pi_agrees_with_pi_on_config_shaped_input(gamma):
     syn = mdp_synth.ell_uniform(300, 4, 8, gamma, seed=5)

@@ -89,3 +89,47 @@ def test_policy_rows_of_the_wrong_action_are_caught(monkeypatch):
     drifting.calls = 0
     monkeypatch.setattr(mo, "policy_matrix", drifting)
     _fails(pins.test_inexact_pi_with_vi_inner_reduces_to_pi_and_vi, 0.9)
+
+
+def _planted_two_level(kind):
+    import scipy.linalg as sla
+    import scipy.sparse as sp
+
+    def bad(mdp, pi, block):
+        J = mo.jacobian(mdp, pi)
+        S = mdp.S
+        agg = np.arange(S) // block
+        if kind == "shift":
+            agg = np.minimum(agg + (np.arange(S) % block == 0), agg[-1])
+        nc = int(agg[-1]) + 1
+        Pr = sp.csr_matrix((np.ones(S), (np.arange(S), agg)), shape=(S, nc))
+        sizes = np.bincount(agg, minlength=nc).astype(np.float64)
+        R = Pr.T.tocsr() if kind == "sum" else sp.diags(1.0 / sizes) @ Pr.T.tocsr()
+        JPr = J @ Pr
+        Jc = np.asarray((R @ JPr).todense() if sp.issparse(JPr) else R @ JPr)
+        lu = sla.lu_factor(Jc)
+        if kind == "no_identity":
+            return R, Pr, Jc, lambda q: Pr @ sla.lu_solve(lu, R @ q)
+        return R, Pr, Jc, lambda q: q + Pr @ sla.lu_solve(lu, R @ q)
+    return bad
+
+
+def test_restriction_that_sums_instead_of_averaging_is_caught(monkeypatch):
+    import oracle
+    monkeypatch.setattr(mo, "two_level", _planted_two_level("sum"))
+    monkeypatch.setattr(oracle, "two_level", mo.two_level)
+    _fails(pins.test_two_level_coarse_operator_is_the_galerkin_product)
+
+
+def test_prolongation_into_the_wrong_block_is_caught(monkeypatch):
+    import oracle
+    monkeypatch.setattr(mo, "two_level", _planted_two_level("shift"))
+    monkeypatch.setattr(oracle, "two_level", mo.two_level)
+    _fails(pins.test_two_level_coarse_operator_is_the_galerkin_product)
+
+
+def test_preconditioner_without_the_identity_term_is_caught(monkeypatch):
+    import oracle
+    monkeypatch.setattr(mo, "two_level", _planted_two_level("no_identity"))
+    monkeypatch.setattr(oracle, "two_level", mo.two_level)
+    _fails(pins.test_preconditioned_gmres_unrestarted_is_exact)
