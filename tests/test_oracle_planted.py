@@ -50,9 +50,9 @@ def test_wrong_sign_in_gram_schmidt_is_caught(monkeypatch):
 def test_restart_that_drops_the_base_is_caught(monkeypatch):
     src = mo._gmres_inner
 
-    def bad(J, g_pi, V_k, Phi_k, threshold, W, max_steps, st):
+    def bad(J, g_pi, V_k, Phi_k, threshold, W, max_steps, st, minv=None):
         # restart from V_k every cycle (forgets the progress of earlier cycles)
-        return src(J, g_pi, V_k, Phi_k, threshold, W, min(max_steps, W), st)
+        return src(J, g_pi, V_k, Phi_k, threshold, W, min(max_steps, W), st, minv)
     monkeypatch.setattr(mo, "_gmres_inner", bad)
     _fails(pins.test_gmres_restarted_converges_to_lu, 2)
 
