@@ -124,6 +124,13 @@ typedef struct {
                         * alpha (Alg. 2); c > 0: alpha_k = min(alpha, c ||Phi_k||_inf), which
                         * tends to 0 (locally Q-superlinear, Sec. 3 theorem), with the inner
                         * threshold alpha_k ||Phi_k||_inf kept >= tol / 10 */
+  int32_t precond_block; /* ipi_solve on ELL data: 0 = plain GMRES (Alg. 2); b = 2^j in
+                        * [4, 2^20] = right-preconditioned inner GMRES with the two-level
+                        * preconditioner M^{-1} q = q + Pr J_c^{-1} R q, where R averages over
+                        * blocks of b consecutive states, Pr copies a block value back and
+                        * J_c = R J^pi Pr (preconditioning is the extension named in Sec. 5).
+                        * Needs at most 8192 blocks and transitions that stay within 31 blocks
+                        * of their state (MDP_EINVAL otherwise).  Other solvers reject it. */
 } mdp_opts;
 
 /* ipi_solve runs each inner GMRES solve as one CUDA-graph launch with a device-side loop.
@@ -132,7 +139,7 @@ typedef struct {
 #define MDP_FLAG_HOST_LOOP 1
 
 /* alpha 0.1, tol 1e-8, restart 30, max_outer 100, max_inner 3000, precision MIXED,
- * opi_W 50, pi_inner_tol_exp 13, flags 0, v0 NULL, forcing_c 0. */
+ * opi_W 50, pi_inner_tol_exp 13, flags 0, v0 NULL, forcing_c 0, precond_block 0. */
 mdp_opts mdp_opts_default(void);
 
 typedef struct {

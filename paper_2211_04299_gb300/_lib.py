@@ -23,7 +23,8 @@ class mdp_opts(C.Structure):
     _fields_ = [("alpha", C.c_double), ("tol", C.c_double), ("restart", C.c_int32),
                 ("max_outer", C.c_int32), ("max_inner", C.c_int32), ("precision", C.c_int32),
                 ("opi_W", C.c_int32), ("pi_inner_tol_exp", C.c_int32), ("flags", C.c_int32),
-                ("v0", C.POINTER(C.c_double)), ("forcing_c", C.c_double)]
+                ("v0", C.POINTER(C.c_double)), ("forcing_c", C.c_double),
+                ("precond_block", C.c_int32)]
 
 
 class mdp_server_opts(C.Structure):

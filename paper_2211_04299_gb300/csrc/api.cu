@@ -95,6 +95,23 @@ struct mdp_s {
   double thr_floor = 0.0;  // and its floor on the inner threshold (tol / 10)
   size_t data_bytes = 0;
   Workspace ws;
+  // two-level preconditioner of ipi_solve (mdp_opts.precond_block): per-policy coarse data
+  struct Precond {
+    int kt = -1, W = 0, lb = -1, bw = -1;
+    int bw_lb = -1;        // aggregation the cached bandwidth was measured for (-1: none)
+    int bw_cached = -1;
+    int64_t nc = 0, ldc = 0;
+    double* band = nullptr;
+    double* scratch = nullptr;
+    float* inv = nullptr;
+    void* E = nullptr;
+    void* ec = nullptr;
+    void* z = nullptr;
+    double* f = nullptr;
+    int* bwbuf = nullptr;
+    size_t bytes = 0;
+  } pc;
+  int pc_on = 0;           // the current solve applies the preconditioner
   // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
   // resumed on the exact residual found by the verifying sweep (rebuilt when parameters change)
   struct InnerGraph {
@@ -102,6 +119,7 @@ struct mdp_s {
     int kt = -1, W = 0, steps = 0;
     double alpha = -1.0, forcing_c = -1.0, thr_floor = -1.0;
     const void* ws = nullptr;
+    const void* pcz = nullptr;  // preconditioner buffers the graph was captured with (or null)
   } ig[2];
   cudaStream_t cap = nullptr;
   std::vector<cudaEvent_t> ev;   // event pool (pairs)
@@ -120,6 +138,18 @@ void free_ws(Workspace& w) {
   if (w.h_sout) cudaFreeHost(w.h_sout);
   if (w.h_ctl) cudaFreeHost(w.h_ctl);
   w = Workspace{};
+}
+
+void free_pc(mdp_s::Precond& p) {
+  void* ptrs[] = {p.band, p.scratch, p.inv, p.E, p.ec, p.z, p.f};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  int* keep = p.bwbuf;
+  const int bl = p.bw_lb, bc = p.bw_cached;
+  p = mdp_s::Precond{};
+  p.bwbuf = keep;
+  p.bw_lb = bl;
+  p.bw_cached = bc;
 }
 
 int alloc0(void** p, size_t bytes, size_t& acc) {
@@ -189,7 +219,98 @@ KrylovBufs kbufs(mdp_t h) {
   B.ctl = w.ctl;
   B.grid = krylov_grid(h);
   B.maxm = w.W + 1;
+  if (h->pc_on) {
+    B.ec = h->pc.ec;
+    B.lb = h->pc.lb;
+  }
   return B;
+}
+
+constexpr int64_t PC_NC_MAX = 8192;  // coarse blocks (J_c^{-1} is nc^2 FP32 values)
+
+// Coarse half-bandwidth of the transition data for blocks of 2^lb states (cached until the
+// data is reloaded).
+int coarse_bandwidth(mdp_t h, int lb, int* bw) {
+  auto& p = h->pc;
+  if (p.bw_lb == lb) {
+    *bw = p.bw_cached;
+    return MDP_OK;
+  }
+  if (!p.bwbuf) {
+    size_t acc = 0;
+    if (cudaMalloc((void**)&p.bwbuf, 64) != cudaSuccess) {
+      cudaGetLastError();
+      p.bwbuf = nullptr;
+      return fail(MDP_ENOMEM, "cudaMalloc failed");
+    }
+    (void)acc;
+  }
+  CK(cudaMemsetAsync(p.bwbuf, 0, sizeof(int), h->stream));
+  RK(launch_coarse_bandwidth(h->d, lb, p.bwbuf, h->stream));
+  int hb = 0;
+  CK(cudaMemcpyAsync(&hb, p.bwbuf, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  p.bw_lb = lb;
+  p.bw_cached = hb;
+  *bw = hb;
+  return MDP_OK;
+}
+
+// Buffers of the two-level preconditioner for Krylov type kt, restart W and blocks of
+// 2^lb states (after ensure_ws).
+int ensure_pc(mdp_t h, int kt, int W, int lb) {
+  auto& p = h->pc;
+  if (h->d.kind != KIND_ELL) return fail(MDP_EINVAL, "the two-level preconditioner needs ELL data");
+  const int64_t S = h->d.S;
+  const int64_t nc = (S + ((int64_t)1 << lb) - 1) >> lb;
+  if (nc > PC_NC_MAX)
+    return fail(MDP_EINVAL, "precond_block too small: more than 8192 coarse blocks");
+  int bw = 0;
+  RK(coarse_bandwidth(h, lb, &bw));
+  if (bw > PC_BW_MAX)
+    return fail(MDP_EINVAL, "transitions reach more than 31 aggregation blocks away: "
+                            "use a larger precond_block");
+  if (p.kt == kt && p.W >= W && p.lb == lb && p.bw == bw && p.inv) return MDP_OK;
+  if (p.inv) CK(cudaStreamSynchronize(h->stream));
+  free_pc(p);
+  p.kt = kt;
+  p.W = W;
+  p.lb = lb;
+  p.bw = bw;
+  p.nc = nc;
+  p.ldc = round_up(nc, 4);
+  const size_t ek = kt ? 4 : 8;
+  size_t& acc = p.bytes;
+  RK(alloc0((void**)&p.band, (size_t)nc * (2 * bw + 1) * 8, acc));
+  RK(alloc0((void**)&p.scratch, (size_t)nc * nc * 8, acc));
+  RK(alloc0((void**)&p.inv, (size_t)nc * nc * 4, acc));
+  RK(alloc0(&p.E, (size_t)W * p.ldc * ek, acc));
+  RK(alloc0(&p.ec, (size_t)p.ldc * ek, acc));
+  RK(alloc0(&p.z, (size_t)h->ws.ldq * ek, acc));
+  RK(alloc0((void**)&p.f, (size_t)p.ldc * 8, acc));
+  return MDP_OK;
+}
+
+PrecondK pck(mdp_t h) {
+  const Workspace& w = h->ws;
+  const auto& p = h->pc;
+  PrecondK k;
+  k.ctl = w.ctl;
+  k.S = h->d.S;
+  k.nc = p.nc;
+  k.ldq = w.ldq;
+  k.ldc = p.ldc;
+  k.lb = p.lb;
+  k.rbuf = w.rbuf;
+  k.w0 = w.w0;
+  k.w1 = w.w1;
+  k.Q = w.Q;
+  k.E = p.E;
+  k.ec = p.ec;
+  k.z = p.z;
+  k.f = p.f;
+  k.inv = p.inv;
+  return k;
 }
 
 // ---------------------------------------------------------------- event timing
@@ -335,6 +456,8 @@ int store_v(mdp_t h, const void* src, double* dst, int arith) {
 }
 
 int enqueue_step(mdp_t h, const int32_t* pi_dev, const void* rhs, cudaStream_t st);
+// Kernels per Arnoldi step as enqueue_step issues them (loop-condition kernel not included).
+int step_launches(mdp_t h) { return h->pc_on ? 10 : 6; }
 
 // One inner solve (Alg. 2 inner loop) on J^pi delta = rhs (rhs already in ws.phi, its norms
 // in ws.sout[slot]), with pi in ws.pi (or pi_dev).  thr: absolute target when alpha == 0.
@@ -356,7 +479,7 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
   RK(read_ctl(h, &hc));
   for (int it = 0; it <= max_steps + 1 && hc.mode != GM_DONE; ++it) {
     RK(enqueue_step(h, pi_dev, rhs ? rhs : w.phi, h->stream));
-    h->launches += 6;
+    h->launches += step_launches(h);
     RK(read_ctl(h, &hc));
   }
   if (hc.mode != GM_DONE) return fail(MDP_ETIMEOUT, "inner GMRES did not reach a final state");
@@ -418,12 +541,19 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, const void* rhs, cudaStream_t s
   C.u = rhs;
   C.out = w.rbuf;
   C.qbase = nullptr;
+  if (h->pc_on) {
+    // right preconditioning: Q_i, R Q_i, E_i = J_c^{-1} R Q_i and z = M^{-1} Q_i first
+    RK(launch_coarse_step(pck(h), w.kt, st));
+    M.x_pre = h->pc.z;
+  }
   RK(launch_matvec(M, st));
   RK(launch_cgs2_givens(B, st));
+  if (h->pc_on) RK(launch_coarse_combine(pck(h), w.kt, st));
   RK(launch_estimate(B, st));
   RK(launch_matvec(C, st));
   return MDP_OK;
 }
+
 
 // Build the graph of one inner solve: prologue (start vector, zero correction, control
 // block), a WHILE node whose body is one Arnoldi step plus the loop-condition kernel, and the
@@ -509,6 +639,7 @@ int build_inner_graph(mdp_t h, int variant, const int32_t* pi_dev, double alpha,
   gg.forcing_c = h->forcing_c;
   gg.thr_floor = h->thr_floor;
   gg.ws = w.ctl;
+  gg.pcz = h->pc_on ? h->pc.z : nullptr;
   return MDP_OK;
 }
 
@@ -518,7 +649,7 @@ int launch_inner_graph(mdp_t h, int variant, double alpha, int W, int max_steps)
   auto& gg = h->ig[variant];
   if (!gg.exec || gg.kt != w.kt || gg.W != W || gg.steps != max_steps || gg.alpha != alpha ||
       gg.forcing_c != h->forcing_c || gg.thr_floor != h->thr_floor ||
-      gg.ws != w.ctl)
+      gg.ws != w.ctl || gg.pcz != (h->pc_on ? h->pc.z : nullptr))
     RK(build_inner_graph(h, variant, w.pi, alpha, W, max_steps));
   CK(cudaGraphLaunch(gg.exec, h->stream));
   return MDP_OK;
@@ -541,8 +672,23 @@ int check_opts(mdp_t h, const mdp_opts& o) {
     return fail(MDP_EINVAL, "unknown precision");
   if (o.precision == MDP_PREC_MIXED && h->d.pdt != MDP_F32)
     return fail(MDP_EINVAL, "mixed precision needs FP32 transition data");
+  if (o.precond_block != 0 &&
+      (o.precond_block < 4 || o.precond_block > (1 << 20) || (o.precond_block & (o.precond_block - 1))))
+    return fail(MDP_EINVAL, "precond_block must be 0 or a power of two in [4, 2^20]");
   return MDP_OK;
 }
+
+int log2_exact(int x) {
+  int l = 0;
+  while ((1 << l) < x) ++l;
+  return l;
+}
+
+// Clears the preconditioner switch of a handle when a solve leaves, on every path.
+struct PcGuard {
+  mdp_t h;
+  ~PcGuard() { h->pc_on = 0; }
+};
 
 double now_s() {
   using namespace std::chrono;
@@ -595,6 +741,11 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
   const int64_t S = h->d.S;
   h->forcing_c = o.forcing_c;
   h->thr_floor = 0.1 * o.tol;
+  PcGuard pc_guard{h};
+  if (o.precond_block) {
+    RK(ensure_pc(h, arith, o.restart, log2_exact(o.precond_block)));
+    h->pc_on = 1;
+  }
   RK(load_v(h, o.v0, arith));
   int status = MDP_ENOCONV;
   SweepOut so{};
@@ -606,6 +757,10 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
     if (k >= o.max_outer) break;
     const double thr = inexact_threshold(o.alpha, o.forcing_c, so.res_inf, h->thr_floor);
     const bool host_loop = (o.flags & MDP_FLAG_HOST_LOOP) != 0;
+    if (h->pc_on) {  // coarse operator of the new policy pi_k: band, LU, explicit inverse
+      RK(launch_coarse_setup(h->d, w.pi, pck(h), h->pc.bw, h->pc.band, h->pc.scratch, h->stream));
+      h->launches += 3;
+    }
     if (host_loop) RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, nullptr, nullptr,
                                   w.phi, 0, 1));
     else RK(launch_inner_graph(h, 0, o.alpha, o.restart, o.max_inner));
@@ -625,7 +780,7 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
       st.bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, w.kt);
       const double avg_m = std::min<double>(o.restart, hc.steps) * 0.5 + 1.0;
       st.bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * (w.kt ? 4.0 : 8.0);
-      h->launches += host_loop ? 0 : 4 + 7 * hc.loop_iters;
+      h->launches += host_loop ? 0 : 4 + (step_launches(h) + 1) * hc.loop_iters;
       // exact stopping test of Alg. 2 (breakdown or the step cap also end the inner loop)
       if (!(sref.res_inf > thr) || hc.status == GS_BREAKDOWN || hc.status == GS_CAP || rep >= 8) break;
       st.restarts += 1;
@@ -734,6 +889,7 @@ int enqueue_upload(mdp_t h, const void* P, const int32_t* col, const double* g,
   DevMDP& d = h->d;
   const size_t eb = d.pdt == MDP_F32 ? 4 : 8;
   cudaStream_t s = h->stream;
+  h->pc.bw_lb = -1;  // new data: the coarse bandwidth is measured again
   if (d.kind == KIND_DENSE) {
     // zero only the pad columns S..ld-1 of every row; the copies below write the rest
     if (d.ld > d.S)
@@ -874,6 +1030,7 @@ mdp_opts mdp_opts_default(void) {
   o.flags = 0;
   o.v0 = nullptr;
   o.forcing_c = 0.0;
+  o.precond_block = 0;
   return o;
 }
 
@@ -924,6 +1081,8 @@ void mdp_destroy(mdp_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
   free_ws(h->ws);
+  free_pc(h->pc);
+  if (h->pc.bwbuf) cudaFree(h->pc.bwbuf);
   void* ptrs[] = {h->P, h->col, h->g64, h->gdf, h->mask, h->gstage, h->vflags};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -995,7 +1154,7 @@ int mdp_info(mdp_t h, int64_t* S, int32_t* A, int32_t* k, int32_t* kind, int32_t
 
 int64_t mdp_device_bytes(mdp_t h) {
   if (!h) return -1;
-  return (int64_t)(h->data_bytes + h->ws.bytes);
+  return (int64_t)(h->data_bytes + h->ws.bytes + h->pc.bytes);
 }
 
 int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double* margin,
@@ -1043,6 +1202,7 @@ int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double t
   mdp_opts o = normalise(opts);
   RK(check_opts(h, o));
   if (!pi || !v_out) return fail(MDP_EINVAL, "null pi or v_out");
+  if (o.precond_block != 0) return fail(MDP_EINVAL, "precond_block applies to ipi_solve only");
   if (!(target_inf >= 0.0)) return fail(MDP_EINVAL, "target must be >= 0");
   const double t0 = now_s();
   mdp_stats st{};
@@ -1090,6 +1250,8 @@ int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double targe
     RK(finish_upload(h));                                                               \
     if (!v_out) return fail(MDP_EINVAL, "null v_out");                                  \
     if (method == METH_OPI && o.opi_W < 1) return fail(MDP_EINVAL, "opi_W must be >= 1");  \
+    if (method != METH_IPI && o.precond_block != 0)                                     \
+      return fail(MDP_EINVAL, "precond_block applies to ipi_solve only");               \
     if (method == METH_IPI) return run_ipi(h, o, v_out, pi_out, stats);                 \
     return run_solver(h, method, o, v_out, pi_out, stats);                              \
   }                                                                                     \

@@ -508,6 +508,7 @@ int check_batch_opts(const mdp_opts& o) {
   if (!(o.alpha > 0.0 && o.alpha < 1.0)) return set_error(MDP_EINVAL, "alpha must be in (0, 1)");
   if (!(o.tol >= 0.0)) return set_error(MDP_EINVAL, "tol must be >= 0");
   if (!(o.forcing_c >= 0.0 && o.forcing_c < INFINITY)) return set_error(MDP_EINVAL, "forcing_c must be finite and >= 0");
+  if (o.precond_block != 0) return set_error(MDP_EINVAL, "precond_block applies to ipi_solve only");
   if (o.max_outer < 0 || o.max_inner < 1) return set_error(MDP_EINVAL, "bad iteration caps");
   if (o.precision != MDP_PREC_MIXED) return set_error(MDP_EINVAL, "a batch runs in MDP_PREC_MIXED");
   if (o.v0) return set_error(MDP_EINVAL, "a batch starts from V_0 = 0 (v0 must be NULL)");

@@ -65,6 +65,7 @@ struct MatvecK {
   int finalize_check;
   void* partials;
   unsigned* counter;
+  const void* x_pre;  // preconditioned STEP: the vector M^{-1} Q_i to multiply (scale 1)
 };
 
 // Resolved per launch (uniform over the grid): input, its scale, output and side output.
@@ -90,10 +91,14 @@ __device__ __forceinline__ MvIO<KT> resolve(const MatvecK& p) {
     io.run = (mode == p.gate_mode || mode == p.gate_mode2);
     if (p.gate_mode == GM_STEP) {
       const int i = c->i;
-      io.x = c->from_rhs ? (const KT*)p.x_rhs : (const KT*)((i - 1) & 1 ? p.x_w1 : p.x_w0);
-      io.scale = scale_of<KT>(c);
       io.out = (KT*)((i & 1) ? p.out1 : p.out0);
-      io.qside = (KT*)p.qbase + (int64_t)i * p.ldq;
+      if (p.x_pre) {  // Q_i was written by the preconditioner's restriction kernel
+        io.x = (const KT*)p.x_pre;
+      } else {
+        io.x = c->from_rhs ? (const KT*)p.x_rhs : (const KT*)((i - 1) & 1 ? p.x_w1 : p.x_w0);
+        io.scale = scale_of<KT>(c);
+        io.qside = (KT*)p.qbase + (int64_t)i * p.ldq;
+      }
     } else {
       io.x = (const KT*)(c->dsel ? p.x_w0 : p.x_w1);  // candidate = dbuf[1 - dsel]
     }
@@ -454,7 +459,7 @@ int launch_mv_typed(const MatvecLaunch& L, cudaStream_t st) {
   MatvecK p{L.d, L.pi, L.x, L.ctl_rw ? L.ctl_rw : const_cast<GmresCtl*>(L.ctl),
             L.gate_mode, L.gate_mode2, L.x_rhs, L.x_w0, L.x_w1, L.qbase, L.ldq,
             L.a, L.b, L.c, L.u, L.out, L.out0, L.out1, L.norms, L.ctl_rw != nullptr,
-            L.partials, L.counter};
+            L.partials, L.counter, L.x_pre};
   const DevMDP& d = L.d;
   if (d.kind == KIND_DENSE) {
     if constexpr (sizeof(PT) == 4 && sizeof(KT) == 4) {
@@ -502,6 +507,8 @@ struct KB {
   void* partials;
   unsigned* counter;
   GmresCtl* ctl;
+  const void* ec;  // two-level preconditioner: coarse part of the candidate (or null)
+  int lb;          // log2 of the aggregation block
 };
 
 
@@ -788,6 +795,26 @@ __device__ __forceinline__ void cgs_axpy_norm_body(const KB& b, GridPos gp) {
   if (threadIdx.x == 0) givens_and_decide(c, sqrt((double)t), sizeof(KT) == 4);
 }
 
+// x + e on the rows of a vector unit that lie below S (the block of 2^lb >= 4 states is the
+// same for every row of the unit; padding rows stay zero).
+template <class KT>
+__device__ __forceinline__ typename TSv<KT>::V add_coarse(typename TSv<KT>::V x, KT e, int64_t r0,
+                                                         int64_t S);
+template <>
+__device__ __forceinline__ float4 add_coarse<float>(float4 x, float e, int64_t r0, int64_t S) {
+  x.x += e;
+  if (r0 + 1 < S) x.y += e;
+  if (r0 + 2 < S) x.z += e;
+  if (r0 + 3 < S) x.w += e;
+  return x;
+}
+template <>
+__device__ __forceinline__ double2 add_coarse<double>(double2 x, double e, int64_t r0, int64_t S) {
+  x.x += e;
+  if (r0 + 1 < S) x.y += e;
+  return x;
+}
+
 // Runs in the modes EST, RESTART and FINISH.  In one pass over Q_0..Q_i it forms the
 // candidate iterate delta_base + sum_{j<=i} y_j Q_j (into dbuf[1 - dsel]) and, in EST mode,
 // the cheap bound r = sum_{j<=i} z_j Q_j + z_{i+1} w / hnext, which equals the residual of the
@@ -833,6 +860,7 @@ __device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp)
         }
       }
     }
+    if (b.ec) x = add_coarse<KT>(x, ((const KT*)b.ec)[(u * T::R) >> b.lb], u * T::R, b.S);
     T::st(cand + u * T::R, x);
     mx = max(mx, T::amax(e));
   }
@@ -1055,7 +1083,8 @@ inline int ew_grid(int64_t n) {
 inline int ok_or_dev() { return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE; }
 
 KB make_kb(const KrylovBufs& B) {
-  return KB{B.S, B.ldq, B.Q, B.w0, B.w1, B.rbuf, B.d0, B.d1, B.partials, B.counter, B.ctl};
+  return KB{B.S, B.ldq, B.Q, B.w0, B.w1, B.rbuf, B.d0, B.d1, B.partials, B.counter, B.ctl,
+            B.ec, B.lb};
 }
 
 }  // namespace
@@ -1114,6 +1143,7 @@ __device__ __forceinline__ MatvecK batch_matvec_params(const BatchInst& I, int w
   p.finalize_check = 0;
   p.partials = I.partials;
   p.counter = I.counter;
+  p.x_pre = nullptr;
   if (which == 1) {
     p.gate_mode = GM_CHECK;
     p.gate_mode2 = GM_RESTART;
@@ -1151,7 +1181,8 @@ __global__ void __launch_bounds__(256) batch_matvec_kernel(BatchDev B, int which
 }
 
 __device__ __forceinline__ KB batch_kb(const BatchInst& I) {
-  return KB{I.d.S, I.ldq, I.Q, I.w0, I.w1, I.rbuf, I.d0, I.d1, I.partials, I.counter, I.ctl};
+  return KB{I.d.S, I.ldq, I.Q, I.w0, I.w1, I.rbuf, I.d0, I.d1, I.partials, I.counter, I.ctl,
+            nullptr, 0};
 }
 
 template <int MAXM, int STAGE>

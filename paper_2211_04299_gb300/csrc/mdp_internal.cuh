@@ -438,6 +438,8 @@ struct MatvecLaunch {
   int grid;
   int* err;
   int no_tma;
+  const void* x_pre;    // gate STEP with a preconditioner: multiply this vector (M^{-1} Q_i,
+                        // already formed) with scale 1 and leave Q_i alone
 };
 
 int launch_matvec(const MatvecLaunch& L, cudaStream_t st);
@@ -457,6 +459,8 @@ struct KrylovBufs {
   GmresCtl* ctl;
   int grid;
   int maxm;       // column capacity of the tall-skinny kernels (>= restart + 1)
+  const void* ec = nullptr;  // two-level preconditioner: coarse part of the candidate, added
+  int lb = 0;                // to each state of its block (block = 2^lb states)
 };
 
 // One Arnoldi step after the matvec: CGS2 (two passes) + norm + Givens + mode decision.
@@ -474,6 +478,36 @@ int launch_loop_cond(cudaGraphConditionalHandle hc, GmresCtl* ctl, int cap, cuda
 int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int max_steps,
                       const SweepOut* rhs_norms, double alpha, cudaStream_t st, int resume = 0,
                       int accept_est = 0, double forcing_c = 0.0, double thr_floor = 0.0);
+
+// Two-level preconditioner (right preconditioning of the inner solve): restriction to blocks
+// of 2^lb consecutive states by averaging, prolongation by copying, Galerkin coarse operator
+// J_c = R J^pi Pr, M^{-1} q = q + Pr J_c^{-1} R q.
+struct PrecondK {
+  const GmresCtl* ctl;
+  int64_t S, nc;        // states, coarse blocks
+  int64_t ldq, ldc;     // leading dimensions of Q (states) and E (coarse blocks)
+  int lb;
+  const void* rbuf;     // Arnoldi-step inputs, as the matvec reads them
+  const void* w0;
+  const void* w1;
+  void* Q;              // [W+1][ldq] Krylov basis (Q_i written here)
+  void* E;              // [W][ldc]: E_i = J_c^{-1} R Q_i
+  void* ec;             // [ldc]: sum_j y_j E_j
+  void* z;              // [ldq]: Q_i + Pr E_i
+  double* f;            // [nc]: R Q_i
+  float* inv;           // [nc][nc]: J_c^{-1}
+};
+constexpr int PC_BW_MAX = 31;  // coarse half-bandwidth handled (one warp lane per band entry)
+// Largest |block(col) - block(s)| over all ELL entries, atomically maxed into *bw (zeroed first).
+int launch_coarse_bandwidth(const DevMDP& d, int lb, int* bw, cudaStream_t st);
+// Per policy: band of J_c (FP64), its banded LU in place, and J_c^{-1} into p.inv.
+// band: nc * (2 bw + 1) doubles; scratch: nc * nc doubles.
+int launch_coarse_setup(const DevMDP& d, const int32_t* pi, const PrecondK& p, int bw,
+                        double* band, double* scratch, cudaStream_t st);
+// Per Arnoldi step (gated on STEP): Q_i and R Q_i, E_i, z = Q_i + Pr E_i.
+int launch_coarse_step(const PrecondK& p, int kt, cudaStream_t st);
+// Gated on EST / RESTART / FINISH: ec = sum_{j <= i} y_j E_j.
+int launch_coarse_combine(const PrecondK& p, int kt, cudaStream_t st);
 
 // Value update v += delta (double or double-float), delta = chosen by ctl (or given).
 int launch_value_update(int kt, void* v, const void* d0, const void* d1, const GmresCtl* ctl,

@@ -337,6 +337,7 @@ int create_server(const mdp_server_opts* opts, mdp_server_s* s) {
   if (!(so.tol >= 0.0)) return set_error(MDP_EINVAL, "tol must be >= 0");
   if (!(so.forcing_c >= 0.0 && so.forcing_c < INFINITY))
     return set_error(MDP_EINVAL, "forcing_c must be finite and >= 0");
+  if (so.precond_block != 0) return set_error(MDP_EINVAL, "precond_block applies to ipi_solve only");
   if (so.max_outer < 0 || so.max_inner < 1) return set_error(MDP_EINVAL, "bad iteration caps");
   if (so.precision != MDP_PREC_MIXED) return set_error(MDP_EINVAL, "the server runs in MDP_PREC_MIXED");
   if (so.v0) return set_error(MDP_EINVAL, "requests start from V_0 = 0 (v0 must be NULL)");

@@ -43,7 +43,7 @@ def test_ctypes_table_matches_header(built):
     assert lib.mdp_version().decode().startswith("mdpgpu")
     o = lib.mdp_opts_default()
     assert o.restart == 30 and abs(o.alpha - 0.1) < 1e-15 and o.precision == 1
-    assert o.forcing_c == 0.0 and not o.v0
+    assert o.forcing_c == 0.0 and not o.v0 and o.precond_block == 0
 
 
 def test_invalid_arguments_fail_before_any_device_work(built):
@@ -73,6 +73,10 @@ def test_invalid_arguments_fail_before_any_device_work(built):
     o.forcing_c = -1.0
     assert lib.mdp_batch_create(one, 1, ctypes.byref(o), ctypes.byref(b)) == _lib.MDP_EINVAL
     assert b"forcing_c" in lib.mdp_last_error()
+    o = lib.mdp_opts_default()
+    o.precond_block = 256  # the two-level preconditioner is an ipi_solve option
+    assert lib.mdp_batch_create(one, 1, ctypes.byref(o), ctypes.byref(b)) == _lib.MDP_EINVAL
+    assert b"precond_block" in lib.mdp_last_error()
     assert not b.value
     assert lib.mdp_batch_solve(None, None, None, None) == _lib.MDP_EINVAL
     assert lib.mdp_batch_solve_dev(None, None, None, None) == _lib.MDP_EINVAL
@@ -93,6 +97,10 @@ def test_invalid_arguments_fail_before_any_device_work(built):
     so = lib.mdp_server_opts_default()
     so.solver.precision = _lib.MDP_PREC_FP64
     assert lib.mdp_server_create(ctypes.byref(so), ctypes.byref(srv)) == _lib.MDP_EINVAL
+    so = lib.mdp_server_opts_default()
+    so.solver.precond_block = 256
+    assert lib.mdp_server_create(ctypes.byref(so), ctypes.byref(srv)) == _lib.MDP_EINVAL
+    assert b"precond_block" in lib.mdp_last_error()
     assert lib.mdp_server_create(None, None) == _lib.MDP_EINVAL
     assert lib.mdp_server_submit(None, 1, 1, 1, None, None, None, 0.9, None, None, None) == _lib.MDP_EINVAL
     assert lib.mdp_server_poll(None, None, None, 0, None) == _lib.MDP_EINVAL

@@ -1,0 +1,169 @@
+"""Two-level preconditioned inner solves (mdp_opts.precond_block) on the GPU.
+
+The oracle's preconditioned iGMRES-PI (right-preconditioned GMRES on J^pi M^{-1} with
+M^{-1} q = q + Pr J_c^{-1} R q over blocks of b consecutive states, the extension named in
+Sec. 5) fixes what the path computes.  A preconditioner changes the Krylov space, not the fixed
+point, so values meet the tolerances of the plain solves (written here, derived as in the
+other parity tests): FP64 within 1e-10 relative with tol tightened so that
+gamma*tol/(1-gamma) stays below it, mixed within 1e-6 relative at ||T(v)-v||_inf <= 1e-8;
+policies bit-exact where the oracle's margin is clear.
+"""
+import numpy as np
+import pytest
+
+import mdp_synth
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mg():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2211_04299_gb300 import build
+    build.build()
+    import paper_2211_04299_gb300 as mg
+    return mg
+
+
+def rel_err(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.max(np.abs(a - b)) / max(1.0, float(np.max(np.abs(b)))))
+
+
+def check_policy(pi_gpu, sw):
+    Q = sw.Q
+    q1 = np.min(Q, axis=0)
+    sure = sw.margin > 1e-9 * np.maximum(1.0, np.abs(q1))
+    assert np.array_equal(np.asarray(pi_gpu)[sure], sw.pi[sure])
+    chosen = Q[np.asarray(pi_gpu), np.arange(Q.shape[1])]
+    assert np.all(chosen - q1 <= 1e-9 * np.maximum(1.0, np.abs(q1)) + 1e-12)
+
+
+def banded(S, prec, seed=1003, halfwidth=512, shift=64):
+    return mdp_synth.ell_banded(S, 16, 32, halfwidth, shift, 0.999, seed=seed,
+                                val_dtype=np.float32 if prec == "mixed" else np.float64)
+
+
+# S=6000: 23 full blocks of 256 and a ragged one of 112; blocks of 64 leave a ragged 48
+# and a coarse half-bandwidth of 17 blocks.
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("block", [256, 64])
+def test_precond_banded_matches_oracle(mg, prec, block):
+    syn = banded(6000, prec)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-11)
+    h = mg.from_synth(syn)
+    tol = 1e-8 if prec == "mixed" else 1e-11
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec, precond_block=block))
+    assert st["status"] == 0 and st["residual_inf"] <= tol, st
+    assert rel_err(v, ref.v) <= (1e-6 if prec == "mixed" else 1e-10)
+    check_policy(pi, oracle.bellman(m, ref.v))
+    # the coarse correction cuts the Krylov work several-fold, as in the oracle
+    _, _, st0 = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec))
+    assert st["inner"] * 2 <= st0["inner"], (st["inner"], st0["inner"])
+    h.close()
+
+
+def test_precond_step_counts_follow_the_oracle(mg):
+    """FP64: the GPU's preconditioned solve stops where the oracle's does, up to the rounding
+    of the estimate that stands in for the true residual."""
+    syn = banded(6000, "fp64")
+    m = oracle.from_synth(syn)
+    ref = oracle.gmres_policy_iteration(m, alpha=0.1, W=30, tol=1e-11, precond_block=256)
+    ref0 = oracle.gmres_policy_iteration(m, alpha=0.1, W=30, tol=1e-11)
+    assert ref.inner * 2 <= ref0.inner
+    h = mg.from_synth(syn)
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-11, precision="fp64", precond_block=256))
+    assert st["status"] == 0
+    assert abs(st["outer"] - ref.outer) <= 2, (st["outer"], ref.outer)
+    assert st["inner"] <= 1.5 * ref.inner + 5, (st["inner"], ref.inner)
+    assert rel_err(v, ref.v) <= 1e-9
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_precond_graph_host_loop_and_reruns_agree(mg, prec):
+    """Every kernel of the preconditioner sums in a fixed order, so the graph-resident loop,
+    the host-driven loop and a second run agree bit for bit."""
+    syn = banded(3000, prec, seed=5, halfwidth=200, shift=40)
+    h = mg.from_synth(syn)
+    tol = 1e-9 if prec == "mixed" else 1e-11
+    o = dict(tol=tol, precision=prec, precond_block=128)
+    v1, pi1, st1 = mg.ipi_solve(h, mg.opts(**o))
+    v2, pi2, st2 = mg.ipi_solve(h, mg.opts(flags=mg.MDP_FLAG_HOST_LOOP, **o))
+    v3, pi3, st3 = mg.ipi_solve(h, mg.opts(**o))
+    for v, pi, st in ((v2, pi2, st2), (v3, pi3, st3)):
+        assert st["status"] == 0
+        np.testing.assert_array_equal(v1, v)
+        np.testing.assert_array_equal(pi1, pi)
+        assert (st1["inner"], st1["outer"]) == (st["inner"], st["outer"])
+    h.close()
+
+
+def test_precond_single_block_and_tiny(mg):
+    """One aggregate (b >= S): J_c is the scalar 1 - gamma (row sums of P^pi are 1), so the
+    coarse correction adds the mean of q / (1 - gamma); and S below a vector unit."""
+    for S, b in ((700, 1024), (3, 4)):
+        syn = mdp_synth.tiny_random(S, 3, seed=S, gamma=0.99, kind="ell", k=min(S, 4),
+                                    density=0.5, val_dtype=np.float64)
+        m = oracle.from_synth(syn)
+        ref = oracle.policy_iteration(m, tol=1e-12)
+        h = mg.from_synth(syn)
+        v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-12, precision="fp64", precond_block=b))
+        assert st["status"] == 0
+        assert rel_err(v, ref.v) <= 1e-9
+        check_policy(pi, oracle.bellman(m, ref.v))
+        h.close()
+
+
+def test_precond_rejections(mg):
+    dense = mdp_synth.tiny_random(50, 2, seed=1, gamma=0.9, kind="dense", val_dtype=np.float64)
+    h = mg.from_synth(dense)
+    with pytest.raises(mg.MDPError, match="ELL"):
+        mg.ipi_solve(h, mg.opts(precision="fp64", precond_block=16))
+    h.close()
+    syn = banded(3000, "fp64", seed=5, halfwidth=200, shift=40)
+    h = mg.from_synth(syn)
+    for bad in (3, 2, 1 << 21, -4):
+        with pytest.raises(mg.MDPError, match="precond_block"):
+            mg.ipi_solve(h, mg.opts(precision="fp64", precond_block=bad))
+    with pytest.raises(mg.MDPError, match="ipi_solve only"):
+        mg.vi_solve(h, mg.opts(precision="fp64", precond_block=64))
+    with pytest.raises(mg.MDPError, match="ipi_solve only"):
+        mg.ipi_vi_solve(h, mg.opts(precision="fp64", precond_block=64))
+    # blocks of 4 states: transitions reach 100+ blocks away
+    with pytest.raises(mg.MDPError, match="31 aggregation blocks"):
+        mg.ipi_solve(h, mg.opts(precision="fp64", precond_block=4))
+    # the handle still solves afterwards
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-10, precision="fp64", precond_block=128))
+    assert st["status"] == 0
+    h.close()
+    big = mdp_synth.ell_banded(40000, 2, 4, 8, 2, 0.9, seed=3, val_dtype=np.float64)
+    h = mg.from_synth(big)
+    with pytest.raises(mg.MDPError, match="8192"):
+        mg.ipi_solve(h, mg.opts(precision="fp64", precond_block=4))
+    h.close()
+
+
+def test_precond_config3_full_size_sampled(mg):
+    """S=10^6, A=16, k=32 banded, FP32 values, gamma=0.999, mixed precision to 1e-8 with blocks
+    of 256 (3907 aggregates): sampled oracle Bellman steps certify the result, and the
+    preconditioned solve needs far fewer Arnoldi steps than the plain one."""
+    syn = mdp_synth.config(3)
+    h = mg.from_synth(syn)
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed", precond_block=256))
+    assert st["status"] == 0 and st["residual_inf"] <= 1e-8, st
+    rng = np.random.default_rng(2)
+    for s in rng.choice(syn.S, 256, replace=False):
+        q = np.array([syn.g[a, s] + syn.gamma * np.dot(syn.val[a, s].astype(np.float64),
+                                                       v[syn.col[a, s]]) for a in range(syn.A)])
+        assert abs(q.min() - v[s]) <= 0.999e-8 * 1.01 + 1e-12 * abs(v[s])
+        two = np.sort(q)[:2]
+        if two[1] - two[0] > 1e-6:
+            assert pi[s] == int(np.argmin(q))
+    _, _, st0 = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed"))
+    assert st["inner"] * 4 <= st0["inner"], (st["inner"], st0["inner"])
+    h.close()
