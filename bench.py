@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--forcing-c", type=float, default=0.0,
                     help="forcing sequence alpha_k = min(alpha, c ||Phi_k||_inf) for the timed "
                          "solves (0 = constant alpha, Alg. 2)")
+    ap.add_argument("--precond-block", type=int, default=0,
+                    help="ELL workloads: two-level preconditioned inner GMRES with aggregation "
+                         "blocks of this many states (0 = plain Alg. 2)")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workload: keep the library's lanes per row (no autotuning), "
                          "so the launch sequence is the same on every run (for profilers)")
@@ -756,7 +759,8 @@ def main():
     torch.cuda.set_stream(stream)
     h.set_stream(stream)
     o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=args.forcing_c,
-                flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0)
+                flags=mg.MDP_FLAG_HOST_LOOP if args.host_loop else 0,
+                precond_block=args.precond_block)
     v_out = torch.empty(S, dtype=torch.float64, device="cuda")
     pi_out = torch.empty(S, dtype=torch.int32, device="cuda")
 
@@ -835,10 +839,32 @@ def main():
         "clocks": clk,
     }
     line["config"]["forcing_c"] = args.forcing_c
+    line["config"]["precond_block"] = args.precond_block
+
+    def timed_variant(ov, n):
+        mg.ipi_solve(h, ov, v_out=v_out, pi_out=pi_out)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        b0.record(stream)
+        for _ in range(n):
+            _, _, stv = mg.ipi_solve(h, ov, v_out=v_out, pi_out=pi_out)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        return n / (b0.elapsed_time(b1) / 1000.0), stv
+
+    # the banded workload with the two-level preconditioned inner solve (blocks of 256
+    # states), for reference beside the plain Alg. 2 line
+    if args.config == 3 and args.precond_block == 0:
+        pb = 256
+        rate, stp = timed_variant(mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
+                                          precond_block=pb), min(args.steps, 10))
+        line["two_level_precond"] = {"precond_block": pb, "value": rate, "unit": "solves/s",
+                                     "outer": stp["outer"], "inner": stp["inner"],
+                                     "converged": stp["status"] == 0 and stp["residual_inf"] <= TOL}
 
     # the same solves with the adaptive forcing sequence (Sec. 3: alpha_k -> 0), for reference
     if args.forcing_c == 0.0:
-        oa = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=1.0)
+        oa = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=1.0,
+                     precond_block=args.precond_block)
         mg.ipi_solve(h, oa, v_out=v_out, pi_out=pi_out)
         na = min(args.steps, 10)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)

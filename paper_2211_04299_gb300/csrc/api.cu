@@ -101,13 +101,15 @@ struct mdp_s {
     int bw_lb = -1;        // aggregation the cached bandwidth was measured for (-1: none)
     int bw_cached = -1;
     int64_t nc = 0, ldc = 0;
-    double* band = nullptr;
-    double* scratch = nullptr;
+    float* band = nullptr;
+    float* cl = nullptr;
+    float* cu = nullptr;
+    float* dinv = nullptr;
     float* inv = nullptr;
     void* E = nullptr;
     void* ec = nullptr;
     void* z = nullptr;
-    double* f = nullptr;
+    float* f = nullptr;
     int* bwbuf = nullptr;
     size_t bytes = 0;
   } pc;
@@ -141,7 +143,7 @@ void free_ws(Workspace& w) {
 }
 
 void free_pc(mdp_s::Precond& p) {
-  void* ptrs[] = {p.band, p.scratch, p.inv, p.E, p.ec, p.z, p.f};
+  void* ptrs[] = {p.band, p.cl, p.cu, p.dinv, p.inv, p.E, p.ec, p.z, p.f};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   int* keep = p.bwbuf;
@@ -281,13 +283,15 @@ int ensure_pc(mdp_t h, int kt, int W, int lb) {
   p.ldc = round_up(nc, 4);
   const size_t ek = kt ? 4 : 8;
   size_t& acc = p.bytes;
-  RK(alloc0((void**)&p.band, (size_t)nc * (2 * bw + 1) * 8, acc));
-  RK(alloc0((void**)&p.scratch, (size_t)nc * nc * 8, acc));
-  RK(alloc0((void**)&p.inv, (size_t)nc * nc * 4, acc));
+  RK(alloc0((void**)&p.band, (size_t)nc * (2 * bw + 3) * 4, acc));
+  RK(alloc0((void**)&p.cl, (size_t)nc * 32 * 4, acc));
+  RK(alloc0((void**)&p.cu, (size_t)nc * 32 * 4, acc));
+  RK(alloc0((void**)&p.dinv, (size_t)nc * 4, acc));
+  RK(alloc0((void**)&p.inv, (size_t)nc * p.ldc * 4, acc));
   RK(alloc0(&p.E, (size_t)W * p.ldc * ek, acc));
   RK(alloc0(&p.ec, (size_t)p.ldc * ek, acc));
   RK(alloc0(&p.z, (size_t)h->ws.ldq * ek, acc));
-  RK(alloc0((void**)&p.f, (size_t)p.ldc * 8, acc));
+  RK(alloc0((void**)&p.f, (size_t)p.ldc * 4, acc));
   return MDP_OK;
 }
 
@@ -758,8 +762,9 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
     const double thr = inexact_threshold(o.alpha, o.forcing_c, so.res_inf, h->thr_floor);
     const bool host_loop = (o.flags & MDP_FLAG_HOST_LOOP) != 0;
     if (h->pc_on) {  // coarse operator of the new policy pi_k: band, LU, explicit inverse
-      RK(launch_coarse_setup(h->d, w.pi, pck(h), h->pc.bw, h->pc.band, h->pc.scratch, h->stream));
-      h->launches += 3;
+      RK(launch_coarse_setup(h->d, w.pi, pck(h), h->pc.bw,
+                             PrecondScratch{h->pc.band, h->pc.cl, h->pc.cu, h->pc.dinv}, h->stream));
+      h->launches += 4;
     }
     if (host_loop) RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, nullptr, nullptr,
                                   w.phi, 0, 1));

@@ -485,7 +485,7 @@ int launch_gmres_init(const KrylovBufs& B, double thr, double sqrtS, int W, int 
 struct PrecondK {
   const GmresCtl* ctl;
   int64_t S, nc;        // states, coarse blocks
-  int64_t ldq, ldc;     // leading dimensions of Q (states) and E (coarse blocks)
+  int64_t ldq, ldc;     // leading dimensions of Q (states) and of E and J_c^{-1} (blocks, % 4 == 0)
   int lb;
   const void* rbuf;     // Arnoldi-step inputs, as the matvec reads them
   const void* w0;
@@ -494,16 +494,24 @@ struct PrecondK {
   void* E;              // [W][ldc]: E_i = J_c^{-1} R Q_i
   void* ec;             // [ldc]: sum_j y_j E_j
   void* z;              // [ldq]: Q_i + Pr E_i
-  double* f;            // [nc]: R Q_i
-  float* inv;           // [nc][nc]: J_c^{-1}
+  float* f;             // [ldc]: R Q_i (zero past nc)
+  float* inv;           // [nc][ldc]: J_c^{-1} (zero past nc in each row)
+};
+// Per-policy setup buffers: the rows of J_c with their row sums and off-diagonal sums, then
+// its LU (nc * (2 bw + 3) floats), and the coefficients of the triangular solves with L and U
+// ([nc][32] floats each, dinv [nc]).
+struct PrecondScratch {
+  float* band;
+  float* cl;
+  float* cu;
+  float* dinv;
 };
 constexpr int PC_BW_MAX = 31;  // coarse half-bandwidth handled (one warp lane per band entry)
 // Largest |block(col) - block(s)| over all ELL entries, atomically maxed into *bw (zeroed first).
 int launch_coarse_bandwidth(const DevMDP& d, int lb, int* bw, cudaStream_t st);
-// Per policy: band of J_c (FP64), its banded LU in place, and J_c^{-1} into p.inv.
-// band: nc * (2 bw + 1) doubles; scratch: nc * nc doubles.
+// Per policy: band of J_c, its banded LU in place, the solve coefficients, J_c^{-1} into p.inv.
 int launch_coarse_setup(const DevMDP& d, const int32_t* pi, const PrecondK& p, int bw,
-                        double* band, double* scratch, cudaStream_t st);
+                        const PrecondScratch& w, cudaStream_t st);
 // Per Arnoldi step (gated on STEP): Q_i and R Q_i, E_i, z = Q_i + Pr E_i.
 int launch_coarse_step(const PrecondK& p, int kt, cudaStream_t st);
 // Gated on EST / RESTART / FINISH: ec = sum_{j <= i} y_j E_j.

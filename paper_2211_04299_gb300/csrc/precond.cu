@@ -7,12 +7,17 @@
 // Galerkin product J_c = R J^pi Pr = I - gamma P_c, P_c row-stochastic, so J_c is a strictly
 // diagonally dominant M-matrix that factors without pivoting.  For transitions that stay within
 // +-bw blocks J_c is banded.  Once per outer iteration (the policy is fixed): build the band,
-// factor it (banded LU, one block), and form J_c^{-1} explicitly in FP32 (one warp per row,
-// solving J_c^T z = e_i with the transposed factors), so that applying the coarse correction in
-// an Arnoldi step is a small dense matvec instead of a sequential triangular solve.  Per step:
+// factor it (banded LU in FP64, one block), and form J_c^{-1} explicitly in FP32 (one warp per
+// row, solving J_c^T z = e_i with the transposed factors), so that the coarse correction in an
+// Arnoldi step is a small dense matvec instead of a sequential triangular solve.  Per step:
 // restrict (write Q_i and its block means), coarse apply (E_i = J_c^{-1} R Q_i), prolong
 // (z = Q_i + Pr E_i, the vector the matvec multiplies).  The candidate iterate adds
-// Pr (sum_j y_j E_j), so M^{-1} is never applied to it separately.
+// Pr (sum_j y_j E_j), the same E_j the Arnoldi process used, so the accuracy of J_c^{-1} only
+// sets how fast the solve converges, never what it converges to.
+//
+// Precision: the band and its LU are FP64 (the pivots of a nearly singular J_c come from
+// cancellation); the triangular solves of the inverse run in FP32, where the M-matrix factors
+// give sums of terms of one sign.  Per-step work is FP32: FP64 throughput is low on this part.
 #include "mdp_internal.cuh"
 
 #include <algorithm>
@@ -22,9 +27,20 @@ namespace mdp {
 namespace {
 
 constexpr int PC_THREADS = 256;
+constexpr int LU_CHUNK = 32;  // rows per cp.async-staged chunk of the banded LU
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_addr(smem)), "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_ahead() {  // all but the newest LU1_AHEAD - 1 groups
+  asm volatile("cp.async.wait_group 7;" ::: "memory");
+}
 
 // Largest |block(col) - block(s)| over every ELL entry of every action (atomicMax).
-template <class PT>
 __global__ void coarse_bandwidth_kernel(DevMDP d, int lb, int* bw) {
   int m = 0;
   const int64_t n = d.S * d.A * (int64_t)d.kp;
@@ -40,118 +56,375 @@ __global__ void coarse_bandwidth_kernel(DevMDP d, int lb, int* bw) {
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(bw, m);
 }
 
-// Band of J_c for coarse row I (one block per coarse row):
-// band[I][t], t = J - I + bw, = delta_{t,bw} - gamma / |I| * sum_{s in I} sum_{c in J} p(s, c).
-// Offsets are summed 8 at a time, each thread over its states in a fixed order and the block
-// by fixed-order reductions, so the band is the same on every run.
+// Row I of the coarse operator (one block per coarse row), stored as Wp = 2 bw + 3 floats:
+//   band[I][t], t = J - I + bw < W:  J_c[I][J] = delta_{IJ} - gamma / |I| * sum_{s in I} sum_{c in J} p(s, c)
+//   band[I][W]:      s_I = row sum of J_c = (1 - gamma) + gamma * mean_{s in I} (1 - sum_c p(s, c))
+//   band[I][W + 1]:  o_I = sum of |J_c[I][J]| over J != I.
+// The row sum is formed from each state's deficit 1 - sum_c p(s, c) (compensated sum), not by
+// cancelling 1 against the row's entries.  A team of PC_TEAM lanes reads one state's row (16-byte
+// loads, as the matvec does); offsets are summed 8 at a time, each lane over its entries in a
+// fixed order, each warp by a fixed shuffle tree, the warps in FP64 in a fixed order, so the
+// row is the same on every run.
+constexpr int PC_TEAM = 8;
 template <class PT>
 __global__ void __launch_bounds__(PC_THREADS) coarse_build_kernel(DevMDP d, const int32_t* pi, int lb,
-                                                                  int bw, double* band) {
-  __shared__ double red[PC_THREADS / 32][8];
-  const int W = 2 * bw + 1;
+                                                                  int bw, float* band) {
+  __shared__ float red[PC_THREADS / 32][9];
+  const int W = 2 * bw + 1, Wp = W + 2;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int team = threadIdx.x / PC_TEAM, tl = threadIdx.x % PC_TEAM;
+  const int nteams = PC_THREADS / PC_TEAM;
   const int64_t I = blockIdx.x;
   const int64_t s0 = I << lb;
   const int64_t cnt = min((int64_t)1 << lb, d.S - s0);
   const PT* val = (const PT*)d.P;
+  const int nvec = d.kp >> 2;
   for (int t0 = 0; t0 < W; t0 += 8) {
-    double part[8];
+    float part[9];  // 8 offsets, and the states' deficits in the first pass
 #pragma unroll
-    for (int q = 0; q < 8; ++q) part[q] = 0.0;
-    for (int64_t u = threadIdx.x; u < cnt; u += blockDim.x) {
-      const int64_t s = s0 + u;
-      const int64_t base = (s * d.A + pi[s]) * d.kp;
-      for (int j = 0; j < d.k; ++j) {
-        const int t = (int)((d.col[base + j] >> lb) - I) + bw - t0;
-        const double x = (double)val[base + j];
+    for (int q = 0; q < 9; ++q) part[q] = 0.f;
+    for (int64_t ub = 0; ub < cnt; ub += nteams) {  // uniform trip count: shuffles below
+      const int64_t u = ub + team;
+      const bool act = u < cnt;
+      float sh = 0.f, sl = 0.f;  // sum_c p(s, c) over this lane's entries (TwoSum cascade)
+      double s64 = 0.0;
+      if (act) {
+        const int64_t s = s0 + u;
+        const int64_t base = (s * d.A + pi[s]) * d.kp;
+        for (int q4 = tl; q4 < nvec; q4 += PC_TEAM) {
+          const int4 c4 = *reinterpret_cast<const int4*>(d.col + base + 4 * q4);
+          PT v[4];
+          if constexpr (sizeof(PT) == 4) {
+            const float4 x = *reinterpret_cast<const float4*>(val + base + 4 * q4);
+            v[0] = x.x; v[1] = x.y; v[2] = x.z; v[3] = x.w;
+          } else {
+            const double2 x0 = *reinterpret_cast<const double2*>(val + base + 4 * q4);
+            const double2 x1 = *(reinterpret_cast<const double2*>(val + base + 4 * q4) + 1);
+            v[0] = x0.x; v[1] = x0.y; v[2] = x1.x; v[3] = x1.y;
+          }
+          const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
 #pragma unroll
-        for (int q = 0; q < 8; ++q) part[q] += (t == q) ? x : 0.0;
+          for (int e = 0; e < 4; ++e) {
+            const int t = (int)((cc[e] >> lb) - I) + bw - t0;
+            const float x = (float)v[e];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) part[q] += (t == q) ? x : 0.f;
+            if (t0 == 0) {
+              if constexpr (sizeof(PT) == 8) {
+                s64 += v[e];
+              } else {
+                const dfl ts = two_sum(sh, x);
+                sh = ts.hi;
+                sl += ts.lo;
+              }
+            }
+          }
+        }
+      }
+      if (t0 == 0) {  // the team's row sum, then the state's deficit 1 - sum
+#pragma unroll
+        for (int o = PC_TEAM / 2; o > 0; o >>= 1) {
+          if constexpr (sizeof(PT) == 8) {
+            s64 += __shfl_xor_sync(0xffffffffu, s64, o);
+          } else {
+            const float h2 = __shfl_xor_sync(0xffffffffu, sh, o);
+            const float l2 = __shfl_xor_sync(0xffffffffu, sl, o);
+            const dfl ts = two_sum(sh, h2);
+            sh = ts.hi;
+            sl = sl + l2 + ts.lo;
+          }
+        }
+        if (act && tl == 0) {
+          if constexpr (sizeof(PT) == 8) {
+            part[8] += (float)(1.0 - s64);
+          } else {
+            const dfl ts = two_sum(1.f, -sh);
+            part[8] += ts.hi + (ts.lo - sl);
+          }
+        }
       }
     }
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const double x = warp_sum(part[q]);
+    for (int q = 0; q < 9; ++q) {
+      const float x = warp_sum(part[q]);
       if (lane == 0) red[wid][q] = x;
     }
     __syncthreads();
-    if (threadIdx.x < 8 && t0 + (int)threadIdx.x < W) {
+    if (threadIdx.x < 9) {
+      const int q = threadIdx.x, t = t0 + q;
       double acc = 0.0;
-      for (int w = 0; w < PC_THREADS / 32; ++w) acc += red[w][threadIdx.x];
-      const int t = t0 + threadIdx.x;
-      band[I * W + t] = (t == bw ? 1.0 : 0.0) - d.gamma * acc / (double)cnt;
+      for (int w = 0; w < PC_THREADS / 32; ++w) acc += (double)red[w][q];
+      if (q < 8 && t < W) band[I * Wp + t] = (float)((t == bw ? 1.0 : 0.0) - d.gamma * acc / (double)cnt);
+      if (q == 8 && t0 == 0)
+        band[I * Wp + W] = (float)((1.0 - d.gamma) + d.gamma * acc / (double)cnt);
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) {  // o_I from the stored (FP32) off-diagonals the LU will use
+    double o = 0.0;
+    for (int t = 0; t < W; ++t)
+      if (t != bw) o -= (double)band[I * Wp + t];
+    band[I * Wp + W + 1] = (float)o;
+  }
 }
 
-// In-place banded LU without pivoting (unit lower L below the diagonal, U on and above);
-// band[i][j - i + bw] holds A[i][j] and no fill leaves the band.  One block; rows k..k+bw live
-// in a shared-memory ring while pivot k is eliminated, and row k is written back when done.
-__global__ void __launch_bounds__(PC_THREADS) coarse_lu_kernel(double* band, int nc, int bw) {
-  extern __shared__ double win[];
-  const int W = 2 * bw + 1, R = bw + 1;
-  for (int e = threadIdx.x; e < R * W; e += blockDim.x) {
-    const int r = e / W;
-    if (r < nc) win[e] = band[(int64_t)r * W + e % W];
-  }
-  __syncthreads();
+// In-place banded LU without pivoting (unit lower L below the diagonal, U on and above) of the
+// M-matrix J_c, in the manner of Grassmann, Taksar and Heyman: every row carries its row sum s
+// and the sum o of its off-diagonal magnitudes over the Schur complement, and the pivot is
+// formed as u_kk = s_k + o_k, so every quantity is a sum of terms of one sign and FP32 keeps
+// its relative accuracy however close J_c is to singular.  Eliminating pivot k, for the rows
+// i = k+1..k+bw:  l_ik = S_ik / u_kk,  s_i += |l_ik| s_k,  o_i += -|S_ik| + |l_ik| (o_k - |u_ki|),
+// S_ij -= l_ik u_kj (i != j; diagonals are never formed until their pivot).
+// One warp: rows k..k+bw live in a shared-memory ring while pivot k is eliminated, lane r owning
+// row k+1+r, so a pivot needs one warp barrier; row k is written back when done and row
+// k+bw+1 taken from a staging buffer that cp.async fills a chunk of rows ahead.
+__global__ void __launch_bounds__(32) coarse_lu_kernel(float* band, int nc, int bw) {
+  extern __shared__ float sm[];
+  const int W = 2 * bw + 1, Wp = W + 2, R = bw + 1;
+  const int lane = threadIdx.x;
+  float* win = sm;             // [R][Wp] ring, row r in slot r % R
+  float* stg = sm + R * Wp;    // [2][LU_CHUNK][Wp]; chunk c holds rows R + c*LU_CHUNK ...
+  const int nstage = nc > R ? (nc - R + LU_CHUNK - 1) / LU_CHUNK : 0;
+  auto issue = [&](int c) {
+    if (c < nstage) {
+      const int r0 = R + c * LU_CHUNK;
+      float* dst = stg + (c & 1) * LU_CHUNK * Wp;
+      for (int rr = 0; rr < LU_CHUNK && r0 + rr < nc; ++rr)
+        for (int t = lane; t < Wp; t += 32)
+          cp_async4(dst + rr * Wp + t, band + (int64_t)(r0 + rr) * Wp + t);
+    }
+    cp_async_commit();  // possibly empty: every lane keeps the same group count
+  };
+  for (int r = 0; r < R && r < nc; ++r)
+    for (int t = lane; t < Wp; t += 32) win[r * Wp + t] = band[(int64_t)r * Wp + t];
+  issue(0);
+  issue(1);
+  __syncwarp();
+  int slot = 0;  // k % R
   for (int k = 0; k < nc; ++k) {
     const int m = min(bw, nc - 1 - k);  // rows / columns of the trailing window
-    double* rk = win + (k % R) * W;
-    const double piv = rk[bw];
-    for (int r = threadIdx.x; r < m; r += blockDim.x) win[((k + 1 + r) % R) * W + (bw - 1 - r)] /= piv;
-    __syncthreads();
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) {
-      const int i = k + 1 + e / m, j = k + 1 + e % m;
-      double* ri = win + (i % R) * W;
-      ri[j - i + bw] -= ri[k - i + bw] * rk[j - k + bw];
+    float* rk = win + slot * Wp;
+    const float sk = rk[W], ok = rk[W + 1];
+    const float u = sk + ok;
+    if (lane < m) {
+      int si = slot + 1 + lane;
+      if (si >= R) si -= R;
+      float* ri = win + si * Wp;
+      const float sik = ri[bw - 1 - lane];  // S_ik <= 0
+      const float l = sik / u;              // l_ik <= 0
+      const float uki = rk[bw + 1 + lane];  // u_ki <= 0
+      ri[bw - 1 - lane] = l;
+      ri[W] = fmaf(-l, sk, ri[W]);
+      ri[W + 1] = fmaxf(0.f, (ri[W + 1] + sik) - l * (ok + uki));
+      // row i = k+1+lane, column j = k+1+c: offset c - lane + bw in row i, c + 1 + bw in row k
+      for (int c = 0; c < m; ++c)
+        if (c != lane) ri[c - lane + bw] = fmaf(-l, rk[c + 1 + bw], ri[c - lane + bw]);
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < W; t += blockDim.x) {
-      band[(int64_t)k * W + t] = rk[t];
-      if (k + R < nc) rk[t] = band[(int64_t)(k + R) * W + t];
+    if (lane == 0) rk[bw] = u;
+    __syncwarp();
+    if (k + R < nc) {
+      const int c = k / LU_CHUNK, o = k % LU_CHUNK;
+      if (o == 0) {  // first row of chunk c: its copies (all but the newest group) are done
+        cp_async_wait1();
+        __syncwarp();
+      }
+      const float* src = stg + (c & 1) * LU_CHUNK * Wp + o * Wp;
+      for (int t = lane; t < Wp; t += 32) {
+        band[(int64_t)k * Wp + t] = rk[t];
+        rk[t] = src[t];
+      }
+      __syncwarp();
+      if (o == LU_CHUNK - 1) issue(c + 2);  // chunk c's buffer is free now
+    } else {
+      for (int t = lane; t < Wp; t += 32) band[(int64_t)k * Wp + t] = rk[t];
+      __syncwarp();
     }
-    __syncthreads();
+    if (++slot == R) slot = 0;
+  }
+  cp_async_wait0();
+}
+
+// Single-thread banded LU for a narrow band (bw = BW <= 8), same elimination (GTH form) as
+// coarse_lu_kernel: the trailing window (rows k..k+BW, columns k..k+2BW) lives in registers, so
+// a pivot is a few dozen FP32 operations with no barrier; rows enter from a shared-memory ring
+// that cp.async fills LU1_AHEAD rows ahead.
+constexpr int LU1_AHEAD = 8;
+template <int BW>
+__global__ void __launch_bounds__(1) coarse_lu1_kernel(float* band, int nc) {
+  constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
+  __shared__ float ring[NS][Wp];
+  float a[R][W];  // a[r][c]: Schur-complement entry (k + r, k + c)
+  float s[R], o[R];
+  auto issue = [&](int i) {  // row i into its ring slot (one commit group, maybe empty)
+    if (i < nc) {
+      float* dst = ring[(i - R) % NS];
+#pragma unroll
+      for (int t = 0; t < Wp; ++t) cp_async4(dst + t, band + (int64_t)i * Wp + t);
+    }
+    cp_async_commit();
+  };
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const bool in = r < nc;
+#pragma unroll
+    for (int c = 0; c < W; ++c) {
+      const int t = c - r + BW;  // row r holds columns r-BW .. r+BW
+      a[r][c] = (in && t >= 0 && t < W) ? band[(int64_t)r * Wp + t] : 0.f;
+    }
+    s[r] = in ? band[(int64_t)r * Wp + W] : 1.f;
+    o[r] = in ? band[(int64_t)r * Wp + W + 1] : 0.f;
+  }
+  for (int q = 0; q < LU1_AHEAD; ++q) issue(R + q);
+  for (int k = 0; k < nc; ++k) {
+    const float u = s[0] + o[0];
+    const float rcp = 1.f / u;
+    float* rowk = band + (int64_t)k * Wp;
+    rowk[BW] = u;
+#pragma unroll
+    for (int c = 1; c <= BW; ++c) rowk[BW + c] = a[0][c];
+#pragma unroll
+    for (int r = 1; r <= BW; ++r) {
+      if (k + r < nc) {
+        const float l = a[r][0] * rcp;
+        band[(int64_t)(k + r) * Wp + BW - r] = l;
+        s[r] = fmaf(-l, s[0], s[r]);
+        o[r] = fmaxf(0.f, (o[r] + a[r][0]) - l * (o[0] + a[0][r]));
+#pragma unroll
+        for (int c = 1; c <= BW; ++c)
+          if (c != r) a[r][c] = fmaf(-l, a[0][c], a[r][c]);
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < BW; ++r) {
+#pragma unroll
+      for (int c = 0; c < W - 1; ++c) a[r][c] = a[r + 1][c + 1];
+      a[r][W - 1] = 0.f;
+      s[r] = s[r + 1];
+      o[r] = o[r + 1];
+    }
+    const int i = k + 1 + BW;  // the row entering the window
+    if (i < nc) {
+      cp_async_wait_ahead();   // row i's group (the oldest pending) is complete
+      const float* src = ring[(i - R) % NS];
+#pragma unroll
+      for (int c = 0; c < W; ++c) a[BW][c] = src[c];
+      s[BW] = src[W];
+      o[BW] = src[W + 1];
+      issue(i + LU1_AHEAD);    // into the slot read one pivot ago
+    } else {
+#pragma unroll
+      for (int c = 0; c < W; ++c) a[BW][c] = 0.f;
+      s[BW] = 1.f;
+      o[BW] = 0.f;
+    }
+  }
+  cp_async_wait0();
+}
+
+// Coefficients of the two triangular solves of J_c x = e_j = L U x, row k of each in a
+// [nc][32] layout (FP32), zero for q >= bw and outside the matrix:
+//   forward  L y = e_j:  y[k] = delta_{kj} + sum_q cl[k][q] y[k-1-q],   cl[k][q] = -L[k][k-1-q]
+//   backward U x = y:    x[k] = dinv[k] y[k] + sum_q cu[k][q] x[k+1+q], cu[k][q] = -U[k][k+1+q] dinv[k]
+__global__ void coarse_prep_kernel(const float* band, int nc, int bw, float* cl, float* cu, float* dinv) {
+  const int W = 2 * bw + 1, Wp = W + 2;
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nc * 32;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int k = (int)(e >> 5), q = (int)(e & 31);
+    const float* rk = band + (int64_t)k * Wp;
+    const float dk = 1.f / rk[bw];
+    float f = 0.f, b = 0.f;
+    if (q < bw) {
+      if (k - 1 - q >= 0) f = -rk[bw - 1 - q];
+      if (k + 1 + q < nc) b = -rk[bw + 1 + q] * dk;
+    }
+    cl[e] = f;
+    cu[e] = b;
+    if (q == 0) dinv[k] = dk;
   }
 }
 
-// Row i of J_c^{-1} is z^T with J_c^T z = e_i; J_c^T = U^T L^T, so first U^T w = e_i (forward,
-// w[k] = 0 for k < i), then L^T z = w (backward).  One warp per row: lane q keeps the value bw
-// steps back that band entry q multiplies, so a step is one warp sum and one shuffle.  The
-// forward values are kept in FP64 scratch (row i) for the backward pass; z is stored in FP32.
-__global__ void __launch_bounds__(PC_THREADS) coarse_inverse_kernel(const double* band, int nc, int bw,
-                                                                    float* inv, double* scratch) {
-  const int lane = threadIdx.x & 31;
-  const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  const int W = 2 * bw + 1;
-  for (int64_t ii = wid; ii < nc; ii += nw) {
-    const int i = (int)ii;
-    double* w = scratch + ii * nc;
-    double r = 0.0;  // lane q: w[k - 1 - q]
-    for (int k = i; k < nc; ++k) {
-      const int j = k - 1 - lane;
-      double t = (lane < bw && j >= i) ? band[(int64_t)j * W + (k - j + bw)] * r : 0.0;
-      t = warp_sum(t);
-      const double nv = ((k == i ? 1.0 : 0.0) - t) / band[(int64_t)k * W + bw];
-      r = __shfl_up_sync(0xffffffffu, r, 1);
-      if (lane == 0) {
-        r = nv;
-        w[k] = nv;
+// Columns of J_c^{-1}: lane j of a warp solves J_c x = e_j for column j = 32 * warp + lane, so
+// all lanes step through k together and read the same coefficients (broadcast), each lane
+// keeping the last RW values of its own recurrence in registers (RW a power of two >= bw; steps
+// are unrolled in blocks of 32 so the ring index is static).  The newest value enters each step
+// through one FMA, so the recurrence runs at FMA latency.  y is parked in inv[k][j] (stores
+// coalesced across lanes) for the backward pass, which reads it a block of 32 steps ahead and
+// overwrites it with x.  With STAGED the block (one warp) first copies the coefficients it
+// needs into shared memory.
+template <int RW, bool STAGED>
+__global__ void __launch_bounds__(32) coarse_inverse_kernel(const float* cl, const float* cu,
+                                                            const float* dinv, int nc, int64_t ldi,
+                                                            float* inv) {
+  extern __shared__ float csm[];  // STAGED: [nc][RW] coefficients, then dinv [nc]
+  const int lane = threadIdx.x;
+  const int64_t j0 = (int64_t)blockIdx.x * 32;
+  const int64_t j = j0 + lane;
+  const bool own = j < nc;
+  auto stage = [&](const float* src, bool with_d) {
+    __syncwarp();
+    for (int64_t e = lane; e < (int64_t)nc * RW; e += 32) csm[e] = src[(e / RW) * 32 + e % RW];
+    if (with_d)
+      for (int64_t e = lane; e < nc; e += 32) csm[(int64_t)nc * RW + e] = dinv[e];
+    __syncwarp();
+  };
+  auto coef = [&](const float* g, int64_t k, int q) -> float {
+    if constexpr (STAGED) return csm[k * RW + q];
+    else return __ldg(g + k * 32 + q);
+  };
+  auto dk = [&](int64_t k) -> float {
+    if constexpr (STAGED) return csm[(int64_t)nc * RW + k];
+    else return __ldg(dinv + k);
+  };
+  if constexpr (STAGED) stage(cl, false);
+  float h[RW];
+#pragma unroll
+  for (int q = 0; q < RW; ++q) h[q] = 0.f;
+  // forward: k = j0 .. nc-1 (y[k] = 0 below the warp's first column)
+  for (int64_t kb = j0; kb < nc; kb += 32) {
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+      const int64_t k = kb + s;
+      if (k < nc) {
+        float part = (k == j) ? 1.f : 0.f;
+#pragma unroll
+        for (int q = 1; q < RW; ++q) part = fmaf(coef(cl, k, q), h[(s - 1 - q) & (RW - 1)], part);
+        const float y = fmaf(coef(cl, k, 0), h[(s - 1) & (RW - 1)], part);
+        h[s & (RW - 1)] = y;
+        if (own) inv[k * ldi + j] = y;
       }
     }
-    r = 0.0;  // lane q: z[k + 1 + q]
-    for (int k = nc - 1; k >= 0; --k) {
-      const int j = k + 1 + lane;
-      double t = (lane < bw && j < nc) ? band[(int64_t)j * W + (k - j + bw)] * r : 0.0;
-      t = warp_sum(t);
-      r = __shfl_up_sync(0xffffffffu, r, 1);
-      if (lane == 0) {
-        const double nv = (k >= i ? w[k] : 0.0) - t;
-        r = nv;
-        inv[ii * nc + k] = (float)nv;
+  }
+  if constexpr (STAGED) stage(cu, true);
+  __syncwarp();
+#pragma unroll
+  for (int q = 0; q < RW; ++q) h[q] = 0.f;
+  // backward: k = nc-1 .. 0, with h[(s - 1 - q) mod RW] holding x[k+1+q]
+  float yb[32];
+  auto load_y = [&](int64_t kb, float (&dst)[32]) {
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+      const int64_t k = kb - s;
+      dst[s] = (k >= j0 && own) ? inv[k * ldi + j] : 0.f;
+    }
+  };
+  load_y(nc - 1, yb);
+  for (int64_t kb = nc - 1; kb >= 0; kb -= 32) {
+    float yn[32];
+    load_y(kb - 32, yn);  // the next block, in flight while this one runs
+#pragma unroll
+    for (int s = 0; s < 32; ++s) {
+      const int64_t k = kb - s;
+      if (k >= 0) {
+        float part = yb[s] * dk(k);
+#pragma unroll
+        for (int q = 1; q < RW; ++q) part = fmaf(coef(cu, k, q), h[(s - 1 - q) & (RW - 1)], part);
+        const float x = fmaf(coef(cu, k, 0), h[(s - 1) & (RW - 1)], part);
+        h[s & (RW - 1)] = x;
+        if (own) inv[k * ldi + j] = x;
       }
     }
+#pragma unroll
+    for (int s = 0; s < 32; ++s) yb[s] = yn[s];
   }
 }
 
@@ -168,18 +441,18 @@ __global__ void __launch_bounds__(PC_THREADS) coarse_restrict_kernel(PrecondK p)
   const int64_t I = blockIdx.x;
   const int64_t s0 = I << p.lb;
   const int64_t cnt = min((int64_t)1 << p.lb, p.S - s0);
-  double sum = 0.0;
+  float sum = 0.f;
   for (int64_t u = threadIdx.x; u < cnt; u += blockDim.x) {
     const KT qs = x[s0 + u] * scale;
     q[s0 + u] = qs;
-    sum += (double)qs;
+    sum += (float)qs;
   }
-  __shared__ double red[32];
+  __shared__ float red[32];
   sum = block_sum(sum, red);
-  if (threadIdx.x == 0) p.f[I] = sum / (double)cnt;
+  if (threadIdx.x == 0) p.f[I] = sum / (float)cnt;
 }
 
-// E_i[I] = sum_J J_c^{-1}[I][J] f[J] (one warp per coarse row).
+// E_i[I] = sum_J J_c^{-1}[I][J] f[J] (one warp per coarse row; rows padded to ldc with zeros).
 template <class KT>
 __global__ void __launch_bounds__(PC_THREADS) coarse_apply_kernel(PrecondK p) {
   const GmresCtl* c = p.ctl;
@@ -188,10 +461,15 @@ __global__ void __launch_bounds__(PC_THREADS) coarse_apply_kernel(PrecondK p) {
   const int64_t wid = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   KT* e = (KT*)p.E + (int64_t)c->i * p.ldc;
+  const float4* f4 = reinterpret_cast<const float4*>(p.f);
+  const int64_t n4 = p.ldc >> 2;
   for (int64_t I = wid; I < p.nc; I += nw) {
-    const float* row = p.inv + I * (int64_t)p.nc;
-    double t = 0.0;
-    for (int64_t J = lane; J < p.nc; J += 32) t += (double)__ldg(row + J) * p.f[J];
+    const float4* row = reinterpret_cast<const float4*>(p.inv + I * p.ldc);
+    float t = 0.f;
+    for (int64_t J = lane; J < n4; J += 32) {
+      const float4 a = __ldg(row + J), b = f4[J];
+      t = fmaf(a.x, b.x, fmaf(a.y, b.y, fmaf(a.z, b.z, fmaf(a.w, b.w, t))));
+    }
     t = warp_sum(t);
     if (lane == 0) e[I] = (KT)t;
   }
@@ -220,9 +498,10 @@ __global__ void coarse_combine_kernel(PrecondK p) {
   const int m = c->i + 1;
   for (int64_t I = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; I < p.nc;
        I += (int64_t)gridDim.x * blockDim.x) {
-    double t = 0.0;
-    for (int j = 0; j < m; ++j) t += c->y[j] * (double)((const KT*)p.E)[(int64_t)j * p.ldc + I];
-    ((KT*)p.ec)[I] = (KT)t;
+    KT t = 0;
+    for (int j = 0; j < m; ++j)
+      t += (sizeof(KT) == 4 ? (KT)c->yf[j] : (KT)c->y[j]) * ((const KT*)p.E)[(int64_t)j * p.ldc + I];
+    ((KT*)p.ec)[I] = t;
   }
 }
 
@@ -233,38 +512,74 @@ inline int pc_grid(int64_t n, int per_block) {
 
 inline int ok() { return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE; }
 
+// Shared memory the staged inverse kernel needs: coefficients [nc][RW] and dinv [nc].
+inline size_t inverse_smem(int64_t nc, int rw) { return (size_t)nc * (rw + 1) * sizeof(float); }
+constexpr size_t INV_SMEM_MAX = 200 * 1024;
+
+template <int RW>
+int launch_inverse(const PrecondScratch& w, const PrecondK& p, cudaStream_t st) {
+  const int grid = (int)((p.nc + 31) / 32);  // one warp (block) per 32 columns
+  const size_t smem = inverse_smem(p.nc, RW);
+  if (smem <= INV_SMEM_MAX) {
+    auto k = coarse_inverse_kernel<RW, true>;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+      return MDP_EDEVICE;
+    k<<<grid, 32, smem, st>>>(w.cl, w.cu, w.dinv, (int)p.nc, p.ldc, p.inv);
+  } else {
+    coarse_inverse_kernel<RW, false><<<grid, 32, 0, st>>>(w.cl, w.cu, w.dinv, (int)p.nc, p.ldc, p.inv);
+  }
+  return MDP_OK;
+}
+
 }  // namespace
 
 int launch_coarse_bandwidth(const DevMDP& d, int lb, int* bw, cudaStream_t st) {
   const int64_t n = d.S * d.A * (int64_t)d.kp;
-  if (d.pdt == MDP_F32) coarse_bandwidth_kernel<float><<<pc_grid(n, 256), 256, 0, st>>>(d, lb, bw);
-  else coarse_bandwidth_kernel<double><<<pc_grid(n, 256), 256, 0, st>>>(d, lb, bw);
+  coarse_bandwidth_kernel<<<pc_grid(n, 256), 256, 0, st>>>(d, lb, bw);
   return ok();
 }
 
+size_t coarse_lu_smem(int bw) { return (size_t)(bw + 1 + 2 * LU_CHUNK) * (2 * bw + 3) * sizeof(float); }
+
 int launch_coarse_setup(const DevMDP& d, const int32_t* pi, const PrecondK& p, int bw,
-                        double* band, double* scratch, cudaStream_t st) {
+                        const PrecondScratch& w, cudaStream_t st) {
   if (d.pdt == MDP_F32)
-    coarse_build_kernel<float><<<(int)p.nc, PC_THREADS, 0, st>>>(d, pi, p.lb, bw, band);
+    coarse_build_kernel<float><<<(int)p.nc, PC_THREADS, 0, st>>>(d, pi, p.lb, bw, w.band);
   else
-    coarse_build_kernel<double><<<(int)p.nc, PC_THREADS, 0, st>>>(d, pi, p.lb, bw, band);
-  const size_t lu_smem = (size_t)(bw + 1) * (2 * bw + 1) * sizeof(double);
-  coarse_lu_kernel<<<1, PC_THREADS, lu_smem, st>>>(band, (int)p.nc, bw);
-  const int grid = (int)std::max<int64_t>(1, (p.nc * 32 + PC_THREADS - 1) / PC_THREADS);
-  coarse_inverse_kernel<<<grid, PC_THREADS, 0, st>>>(band, (int)p.nc, bw, p.inv, scratch);
+    coarse_build_kernel<double><<<(int)p.nc, PC_THREADS, 0, st>>>(d, pi, p.lb, bw, w.band);
+  switch (bw) {  // a narrow band factors in one thread's registers
+    case 1: coarse_lu1_kernel<1><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 2: coarse_lu1_kernel<2><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 3: coarse_lu1_kernel<3><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 4: coarse_lu1_kernel<4><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 5: coarse_lu1_kernel<5><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 6: coarse_lu1_kernel<6><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 7: coarse_lu1_kernel<7><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    case 8: coarse_lu1_kernel<8><<<1, 1, 0, st>>>(w.band, (int)p.nc); break;
+    default: coarse_lu_kernel<<<1, 32, coarse_lu_smem(bw), st>>>(w.band, (int)p.nc, bw);
+  }
+  coarse_prep_kernel<<<pc_grid(p.nc * 32, 256), 256, 0, st>>>(w.band, (int)p.nc, bw, w.cl, w.cu, w.dinv);
+  int r;
+  if (bw <= 2) r = launch_inverse<2>(w, p, st);
+  else if (bw <= 4) r = launch_inverse<4>(w, p, st);
+  else if (bw <= 8) r = launch_inverse<8>(w, p, st);
+  else if (bw <= 16) r = launch_inverse<16>(w, p, st);
+  else r = launch_inverse<32>(w, p, st);
+  if (r != MDP_OK) return r;
   return ok();
 }
 
 int launch_coarse_step(const PrecondK& p, int kt, cudaStream_t st) {
-  const int gapply = (int)std::min<int64_t>((p.nc * 32 + PC_THREADS - 1) / PC_THREADS,
-                                            (int64_t)num_sms() * 8);
+  const int gapply = (int)std::max<int64_t>(1, std::min<int64_t>((p.nc * 32 + PC_THREADS - 1) / PC_THREADS,
+                                                                  (int64_t)num_sms() * 8));
   if (kt == 1) {
     coarse_restrict_kernel<float><<<(int)p.nc, PC_THREADS, 0, st>>>(p);
-    coarse_apply_kernel<float><<<std::max(1, gapply), PC_THREADS, 0, st>>>(p);
+    coarse_apply_kernel<float><<<gapply, PC_THREADS, 0, st>>>(p);
     coarse_prolong_kernel<float><<<pc_grid(p.S, 256), 256, 0, st>>>(p);
   } else {
     coarse_restrict_kernel<double><<<(int)p.nc, PC_THREADS, 0, st>>>(p);
-    coarse_apply_kernel<double><<<std::max(1, gapply), PC_THREADS, 0, st>>>(p);
+    coarse_apply_kernel<double><<<gapply, PC_THREADS, 0, st>>>(p);
     coarse_prolong_kernel<double><<<pc_grid(p.S, 256), 256, 0, st>>>(p);
   }
   return ok();
