@@ -67,6 +67,9 @@ def parse():
     ap.add_argument("--precond-block", type=int, default=0,
                     help="ELL workloads: two-level preconditioned inner GMRES with aggregation "
                          "blocks of this many states (0 = plain Alg. 2)")
+    ap.add_argument("--study", choices=["fig2"], default=None,
+                    help="fig2: GMRES vs VI policy evaluation across gamma at n=100 (Sec. 3.1): "
+                         "Arnoldi steps, VI sweeps and times on the GPU; one JSON line")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workload: keep the library's lanes per row (no autotuning), "
                          "so the launch sequence is the same on every run (for profilers)")
@@ -723,6 +726,34 @@ def run_serve_bench(args, mg, torch, dist, world, rank, local):
 
 
 # ---------------------------------------------------------------- GPU arm
+def run_fig2_study(mg, torch, rank):
+    """Fig. 2 (Sec. 3.1): policy evaluation of a dense n=100 MDP (one action, rows
+    Dirichlet(1)) to ||g - J V||_inf <= 1e-8 by GMRES(64) and by VI, for several gamma (the
+    counts are checked against the oracle in the GPU tests)."""
+    import mdp_synth
+    rows = []
+    for g in (0.5, 0.9, 0.99, 0.999, 0.9999):
+        syn = mdp_synth.dense_dirichlet(100, 1, 1.0, g, seed=2022, dtype=np.float64)
+        h = mg.from_synth(syn)
+        pi0 = np.zeros(100, np.int32)
+        og = mg.opts(precision="fp64", restart=64)
+        ov = mg.opts(precision="fp64", tol=1e-8, max_outer=10 ** 7)
+        mg.policy_eval_gmres(h, pi0, target_inf=1e-8, o=og)
+        t0 = time.perf_counter()
+        _, st_g = mg.policy_eval_gmres(h, pi0, target_inf=1e-8, o=og)
+        t1 = time.perf_counter()
+        _, _, st_v = mg.vi_solve(h, ov)
+        t2 = time.perf_counter()
+        h.close()
+        rows.append({"gamma": g, "gmres_steps": st_g["inner"], "vi_sweeps": st_v["outer"],
+                     "converged": st_g["status"] == 0 and st_v["status"] == 0,
+                     "gmres_ms": 1e3 * (t1 - t0), "vi_ms": 1e3 * (t2 - t1)})
+    if rank == 0:
+        print(json.dumps({"study": "fig2", "n": 100, "target_inf": 1e-8, "data": "synthetic",
+                          "rows": rows}), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -740,6 +771,8 @@ def main():
     import paper_2211_04299_gb300 as mg
     import mdp_synth
 
+    if args.study == "fig2":
+        return run_fig2_study(mg, torch, rank)
     if args.config == 4:
         return run_batch_bench(args, mg, torch, dist, world, rank, local)
     if args.config == 5:

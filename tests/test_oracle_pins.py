@@ -476,3 +476,25 @@ def test_paper_qualitative_ordering():
     o5 = oracle.optimistic_policy_iteration(m, W=5, tol=1e-8)
     o20 = oracle.optimistic_policy_iteration(m, W=20, tol=1e-8)
     assert pi.outer <= ig.outer <= o20.outer <= o5.outer
+
+
+def test_gmres_steps_robust_to_gamma_vi_sweeps_not():
+    """Fig. 2 (Sec. 3.1): policy evaluation at n = 100 by GMRES needs about the same number
+    of Arnoldi steps from gamma = 0.5 to 0.999 (spectrum lemma: the eigenvalues of
+    I - gamma P^pi lie in the disc of radius gamma around 1, and for a well-mixed P^pi all but
+    one cluster near 1), while VI needs log(tol)/log(gamma) sweeps up to a constant: the
+    Perron component of the residual shrinks by exactly gamma per sweep."""
+    steps, sweeps = [], []
+    for g in (0.5, 0.9, 0.99, 0.999):
+        syn = mdp_synth.dense_dirichlet(100, 1, 1.0, g, seed=2022, dtype=np.float64)
+        m = oracle.from_synth(syn)
+        pi0 = np.zeros(100, np.int32)
+        rg = oracle.policy_eval_gmres(m, pi0, target_inf=1e-8, W=64)
+        rv = oracle.value_iteration(m, tol=1e-8, max_iter=10 ** 6)
+        steps.append(rg.inner)
+        sweeps.append(rv.outer)
+        # VI: ||Phi_k||_inf >= gamma^k * |Perron component| with ||Phi_0|| = ||g|| <= 1
+        assert rv.outer >= np.log(1e-8) / np.log(g) - np.log(1e3) / -np.log(g) - 1
+        assert rv.outer <= np.log(1e-8) / np.log(g) + 5 / (1 - g)
+    assert steps[-1] <= 2 * steps[0] + 2 and max(steps) <= 100
+    assert sweeps[-1] >= 100 * sweeps[0]
