@@ -14,6 +14,7 @@ MDP_OK, MDP_EINVAL, MDP_ENOMEM, MDP_ENOCONV, MDP_EDEVICE, MDP_ETIMEOUT = 0, -1, 
 MDP_F32, MDP_F64 = 0, 1
 MDP_PREC_FP64, MDP_PREC_MIXED = 0, 1
 MDP_FLAG_HOST_LOOP = 1
+MDP_FLAG_NO_WINDOW = 2
 
 STATUS_NAMES = {0: "ok", -1: "einval", -2: "enomem", -3: "enoconv", -4: "edevice",
                 -5: "etimeout", 1: "breakdown"}

@@ -114,6 +114,7 @@ struct mdp_s {
     size_t bytes = 0;
   } pc;
   int pc_on = 0;           // the current solve applies the preconditioner
+  int no_window = 0;       // the current solve asked for the global-gather ELL sweep
   // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
   // resumed on the exact residual found by the verifying sweep (rebuilt when parameters change)
   struct InnerGraph {
@@ -395,6 +396,7 @@ int sweep(mdp_t h, int arith, const void* v, const int32_t* pi_in, int32_t* pi_o
   L.err = h->ws.flags + 8;
   L.lanes = h->lanes_sweep;
   L.grid = pi_in ? 0 : h->grid_sweep;
+  L.no_window = h->no_window || h->grid_sweep > 0;  // a fixed geometry is the batch's
   int t = tic(h, pi_in ? 1 : 0);
   int r = launch_sweep(L, h->stream);
   toc(h, t);
@@ -688,10 +690,10 @@ int log2_exact(int x) {
   return l;
 }
 
-// Clears the preconditioner switch of a handle when a solve leaves, on every path.
+// Clears the per-solve switches of a handle when a solve leaves, on every path.
 struct PcGuard {
   mdp_t h;
-  ~PcGuard() { h->pc_on = 0; }
+  ~PcGuard() { h->pc_on = 0; h->no_window = 0; }
 };
 
 double now_s() {
@@ -895,6 +897,7 @@ int enqueue_upload(mdp_t h, const void* P, const int32_t* col, const double* g,
   const size_t eb = d.pdt == MDP_F32 ? 4 : 8;
   cudaStream_t s = h->stream;
   h->pc.bw_lb = -1;  // new data: the coarse bandwidth is measured again
+  d.span = -1;
   if (d.kind == KIND_DENSE) {
     // zero only the pad columns S..ld-1 of every row; the copies below write the rest
     if (d.ld > d.S)
@@ -948,6 +951,7 @@ int finish_upload(mdp_t h) {
   if (hf[2]) return fail(MDP_EINVAL, "a transition row does not sum to 1 within tolerance");
   if (hf[3]) return fail(MDP_EINVAL, "costs must be finite");
   if (hf[4]) return fail(MDP_EINVAL, "every state needs at least one allowed action");
+  h->d.span = h->d.kind == KIND_ELL ? hf[6] : -1;  // column reach: banded data sweeps windowed
   return MDP_OK;
 }
 
@@ -977,6 +981,7 @@ int create_common(int64_t S, int32_t A, int32_t k, int kind, const void* P, int 
   d.gamma = gamma;
   d.gamma_hi = (float)gamma;
   d.gamma_lo = (float)(gamma - (double)d.gamma_hi);
+  d.span = -1;  // measured by the validation of each upload
   const size_t eb = dt == MDP_F32 ? 4 : 8;
   size_t acc = 0;
   int r = MDP_OK;
@@ -1209,6 +1214,8 @@ int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double t
   if (!pi || !v_out) return fail(MDP_EINVAL, "null pi or v_out");
   if (o.precond_block != 0) return fail(MDP_EINVAL, "precond_block applies to ipi_solve only");
   if (!(target_inf >= 0.0)) return fail(MDP_EINVAL, "target must be >= 0");
+  PcGuard guard{h};
+  h->no_window = (o.flags & MDP_FLAG_NO_WINDOW) != 0;
   const double t0 = now_s();
   mdp_stats st{};
   h->launches = 0;
@@ -1257,6 +1264,8 @@ int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double targe
     if (method == METH_OPI && o.opi_W < 1) return fail(MDP_EINVAL, "opi_W must be >= 1");  \
     if (method != METH_IPI && o.precond_block != 0)                                     \
       return fail(MDP_EINVAL, "precond_block applies to ipi_solve only");               \
+    PcGuard guard{h};                                                                   \
+    h->no_window = (o.flags & MDP_FLAG_NO_WINDOW) != 0;                                 \
     if (method == METH_IPI) return run_ipi(h, o, v_out, pi_out, stats);                 \
     return run_solver(h, method, o, v_out, pi_out, stats);                              \
   }                                                                                     \

@@ -983,7 +983,7 @@ __global__ void validate_kernel(DevMDP d, int* flags) {
   const int64_t nrows = d.S * d.A;
   const PT* P = (const PT*)d.P;
   const double tol = 1e-5;  // FP32 rows keep their ~1e-7 rounding
-  int badv = 0, badc = 0, bads = 0;
+  int badv = 0, badc = 0, bads = 0, span = 0;
   if (d.kind == KIND_DENSE) {
     const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
     const int64_t nv = d.ld / 4;
@@ -1036,10 +1036,19 @@ __global__ void validate_kernel(DevMDP d, int* flags) {
         }
         tot = sm;
       }
+      const int64_t s = r / d.A;
       for (int q = 0; q < nv; ++q) {
         const int4 c = __ldcs(cr + q);
         badc |= (c.x < 0 || c.x >= d.S) | (c.y < 0 || c.y >= d.S) | (c.z < 0 || c.z >= d.S) |
                 (c.w < 0 || c.w >= d.S);
+        const int cc[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+        for (int e = 0; e < 4; ++e)  // column reach of the stored entries (pads excluded)
+          if (4 * q + e < d.k) {
+            const int64_t dl = (int64_t)cc[e] - s;
+            const int64_t ad = dl < 0 ? -dl : dl;
+            span = max(span, ad > INT_MAX ? INT_MAX : (int)ad);
+          }
       }
       if (!(fabs(tot - 1.0) <= tol)) bads = 1;
     }
@@ -1047,7 +1056,9 @@ __global__ void validate_kernel(DevMDP d, int* flags) {
   badv = __any_sync(0xffffffffu, badv);
   badc = __any_sync(0xffffffffu, badc);
   bads = __any_sync(0xffffffffu, bads);
+  span = warp_max(span);
   if (lane == 0) {
+    if (span > 0) atomicMax(flags + 6, span);
     if (badv) atomicOr(flags + 0, 1);
     if (badc) atomicOr(flags + 1, 1);
     if (bads) atomicOr(flags + 2, 1);

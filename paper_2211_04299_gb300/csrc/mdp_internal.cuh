@@ -40,6 +40,7 @@ struct DevMDP {
   const double* g64;   // [S][A]
   const float2* gdf;   // [S][A] double-float copy (FP32 P only)
   const uint8_t* mask; // [S][A] or null
+  int64_t span;        // ELL: max |col - s| over the stored entries (set by validation); -1 unknown
 };
 
 // ------------------------------------------------------------------ double-float arithmetic
@@ -408,6 +409,7 @@ struct SweepLaunch {
   int grid;             // 0 = choose
   int* err;             // raised by a bounded wait that ran out (bulk-copy kernels)
   int no_tma;           // force the register-streaming kernel
+  int no_window;        // ELL: force the global-gather kernel even for banded columns
 };
 
 int launch_sweep(const SweepLaunch& L, cudaStream_t st);
@@ -527,7 +529,8 @@ int launch_fill_zero(void* p, size_t bytes, cudaStream_t st);
 // Transpose [A][S] -> [S][A] for g (and produce the double-float copy when gdf != null).
 int launch_cost_transpose(const double* gAS, double* gSA, float2* gdf, int64_t S, int32_t A,
                           cudaStream_t st);
-// Device-side validation of uploaded data; writes error flags into *flags (4 ints).
+// Device-side validation of uploaded data: error flags into flags[0..4] (values, columns, row
+// sums, costs, allowed actions) and, for ELL, the largest |col - s| into flags[6] (atomicMax).
 int launch_validate(const DevMDP& d, int* flags, cudaStream_t st);
 // flags[5] |= 1 when a policy entry is out of range or disallowed by the mask.
 int launch_check_policy(const int32_t* pi, int64_t S, int32_t A, const uint8_t* mask, int* flags,

@@ -144,6 +144,7 @@ DevMDP request_view(int64_t S, int32_t A, int32_t k, double gamma) {
   d.gamma = gamma;
   d.gamma_hi = (float)gamma;
   d.gamma_lo = (float)(gamma - (double)d.gamma_hi);
+  d.span = -1;
   return d;
 }
 

@@ -683,109 +683,272 @@ __device__ __forceinline__ Cand<AR> cand_shfl(const Cand<AR>& x, int off) {
   return r;
 }
 
-template <class PT, class AR, int T>
-__device__ __forceinline__ void sweep_ell_body(const SweepK& p, GridPos gp) {
-  using V = typename AR::V;
+// Lane roles of the ELL sweep (fixed for a launch).
+struct EllLanes {
+  int R, Rp, G, npass, rr, tl, g, leader, nvec, T;
+};
+
+template <int T>
+__device__ __forceinline__ EllLanes ell_lanes(const SweepK& p) {
+  EllLanes L;
+  const int lane = threadIdx.x & 31;
+  L.R = p.pi_in ? 1 : p.d.A;
+  constexpr int RPI = 32 / T;                      // row slots per pass
+  L.Rp = 1;
+  while (L.Rp < L.R && L.Rp < RPI) L.Rp <<= 1;     // row slots of one state per pass
+  L.G = RPI / L.Rp;                                // states per pass
+  L.npass = (L.R + RPI - 1) / RPI;                 // passes per state
+  const int row_slot = lane / T;
+  L.tl = lane % T;
+  L.g = row_slot / L.Rp;
+  L.rr = row_slot % L.Rp;
+  L.leader = L.g * L.Rp * T;
+  L.nvec = p.d.kp >> 2;
+  L.T = T;
+  return L;
+}
+
+// Gathers of v at a column: from global memory with an L2 evict-last hint, or from a block's
+// shared-memory window of v.
+template <class AR> struct GatherGlobal {
+  const typename AR::V* v;
+  uint64_t pol;
+  __device__ __forceinline__ typename AR::V operator()(int c) const { return ld_keep(v + c, pol); }
+};
+template <class AR> struct GatherRing {
+  const typename AR::V* ring;
+  int mask;
+  __device__ __forceinline__ typename AR::V operator()(int c) const { return ring[c & mask]; }
+};
+
+// Merge without the second-best value (when no margin is asked for).
+template <class AR>
+__device__ __forceinline__ Cand<AR> cand_merge1(const Cand<AR>& x, const Cand<AR>& y) {
+  const bool xfirst = AR::lt(x.q, y.q) || (!AR::lt(y.q, x.q) && x.a < y.a);
+  Cand<AR> r;
+  r.q = xfirst ? x.q : y.q;
+  r.a = xfirst ? x.a : y.a;
+  r.q2 = x.q2;
+  return r;
+}
+template <class AR>
+__device__ __forceinline__ Cand<AR> cand_shfl1(const Cand<AR>& x, int off) {
+  Cand<AR> r;
+  r.q = shfl_xor_q<AR>(x.q, off);
+  r.q2 = x.q2;
+  r.a = __shfl_xor_sync(0xffffffffu, x.a, off);
+  return r;
+}
+
+// One group of G states starting at s0 (every lane of the warp takes part): the Q-values of
+// their rows and the argmin.  Returns the state's pick in every lane of its row group.
+template <class PT, class AR, int T, class Gather>
+__device__ __forceinline__ Pick<AR> ell_state_group(const SweepK& p, const EllLanes& L, int64_t s0,
+                                                    const Gather& gather) {
   using Qt = typename AR::Qt;
+  using V = typename AR::V;
   const DevMDP& d = p.d;
+  constexpr int RPI = 32 / T;
+  const PT* val = (const PT*)d.P;
+  const int32_t* col = d.col;
+  const int64_t s = s0 + L.g;
+  const bool st_ok = s < d.S;
+  const bool need_q2 = p.margin_out != nullptr;
+  Cand<AR> run;
+  run.q = AR::inf(); run.q2 = AR::inf(); run.a = 0x7fffffff;
+  Qt qref = AR::inf();
+  const int aref = (p.pi_ref && st_ok) ? p.pi_ref[s] : -1;
+  for (int pass = 0; pass < L.npass; ++pass) {
+    const int a_local = pass * RPI + L.rr;
+    const bool act = st_ok && a_local < L.R;
+    const int a = act ? (p.pi_in ? p.pi_in[s] : a_local) : 0;
+    typename AR::Acc acc;
+    acc.init();
+    if (act) {
+      const int64_t base = ((int64_t)s * d.A + a) * d.kp;
+      for (int q0 = L.tl; q0 < L.nvec; q0 += 2 * T) {
+        Vec4<PT> pv[2];
+        int4 c4[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int q = q0 + b * T;
+          if (q < L.nvec) {
+            pv[b].load(val + base + 4 * q);
+            c4[b] = __ldcs(reinterpret_cast<const int4*>(col + base) + q);
+          } else {
+            c4[b] = make_int4(0, 0, 0, 0);
+#pragma unroll
+            for (int e = 0; e < 4; ++e) pv[b].e[e] = PT(0);
+          }
+        }
+        V x[8];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          x[4 * b + 0] = gather(c4[b].x);
+          x[4 * b + 1] = gather(c4[b].y);
+          x[4 * b + 2] = gather(c4[b].z);
+          x[4 * b + 3] = gather(c4[b].w);
+        }
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) acc.add(pv[b].e[e], x[4 * b + e]);
+        }
+        acc.tick2();
+      }
+    }
+    const Qt sum = AR::reduce_team(acc.result(), T);
+    const Qt q = act ? AR::qval(d, s, a, sum) : AR::inf();
+    const bool allowed = act && (p.pi_in ? true : (d.mask ? d.mask[s * d.A + a] != 0 : true));
+    // reference-policy row of this pass (when it lies here): its lane holds qref.  Every
+    // lane takes part in the shuffle; only lanes whose reference row is in this pass keep it.
+    if (p.pi_ref) {
+      const int aoff = aref - pass * RPI;
+      const bool here = aref >= 0 && aoff >= 0 && aoff < L.Rp && aref < L.R;
+      const Qt qs = shfl_q<AR>(q, L.leader + (here ? aoff : 0) * T);
+      if (here) qref = qs;
+    }
+    Cand<AR> c;
+    c.q = allowed ? q : AR::inf();
+    c.q2 = AR::inf();
+    c.a = allowed ? a : 0x7fffffff;
+    if (need_q2) {
+      for (int off = T; off < L.Rp * T; off <<= 1) c = cand_merge<AR>(c, cand_shfl<AR>(c, off));
+      run = cand_merge<AR>(run, c);
+    } else {
+      for (int off = T; off < L.Rp * T; off <<= 1) c = cand_merge1<AR>(c, cand_shfl1<AR>(c, off));
+      run = cand_merge1<AR>(run, c);
+    }
+  }
+  Pick<AR> pk;
+  pk.best = run.q;
+  pk.second = run.q2;
+  pk.abest = p.pi_in ? (st_ok ? p.pi_in[s] : 0) : (run.a == 0x7fffffff ? -1 : run.a);
+  pk.qref = qref;
+  return pk;
+}
+
+// Per-state outputs leave 32 states at a time: each group's pick is handed to one lane of
+// the warp (in order), and when every lane holds one the warp writes them in parallel
+// (consecutive lanes, mostly consecutive states) instead of one lane writing per state.
+template <class AR>
+struct EmitQueue {
+  Pick<AR> pk;
+  int64_t s;
+  int n;
+  __device__ __forceinline__ void init() { s = -1; n = 0; }
+  __device__ __forceinline__ void flush(const SweepK& p, Norms<AR>& nm) {
+    if (s >= 0 && s < p.d.S) emit_state<AR>(p, s, pk, nm);
+    s = -1;
+    n = 0;
+  }
+  __device__ __forceinline__ void push(const SweepK& p, const EllLanes& L, int64_t s0,
+                                       const Pick<AR>& in, Norms<AR>& nm) {
+    const int lane = threadIdx.x & 31;
+    for (int g = 0; g < L.G; ++g) {
+      const int src = g * L.Rp * L.T;
+      Pick<AR> x;
+      x.best = shfl_q<AR>(in.best, src);
+      x.second = p.margin_out ? shfl_q<AR>(in.second, src) : in.second;
+      x.qref = p.pi_ref ? shfl_q<AR>(in.qref, src) : in.qref;
+      x.abest = __shfl_sync(0xffffffffu, in.abest, src);
+      if (lane == n) {
+        pk = x;
+        s = s0 + g;
+      }
+      if (++n == 32) flush(p, nm);
+    }
+  }
+};
+
+// QUEUE: hand the outputs to the emit queue (fewer instructions, ~10 more registers), or
+// write each group's outputs from its leader lane right away (the batched kernel, whose
+// staged instance record leaves no registers to spare).
+template <class PT, class AR, int T, bool QUEUE = true>
+__device__ __forceinline__ void sweep_ell_body(const SweepK& p, GridPos gp) {
+  const EllLanes L = ell_lanes<T>(p);
   const int lane = threadIdx.x & 31;
   const int64_t gw = ((int64_t)gp.bid * blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = (int64_t)gp.nb * (blockDim.x >> 5);
-  const int R = p.pi_in ? 1 : d.A;
-  constexpr int RPI = 32 / T;                  // row slots per pass
-  int Rp = 1;
-  while (Rp < R && Rp < RPI) Rp <<= 1;         // row slots of one state per pass
-  const int G = RPI / Rp;                      // states per pass
-  const int npass = (R + RPI - 1) / RPI;       // passes per state
-  const int row_slot = lane / T, tl = lane % T;
-  const int g = row_slot / Rp, rr = row_slot % Rp;
-  const int leader = g * Rp * T;
-  const PT* val = (const PT*)d.P;
-  const int32_t* col = d.col;
-  const V* v = (const V*)p.v;
-  const int nvec = d.kp >> 2;
-  const uint64_t pol = l2_keep_policy();
+  const GatherGlobal<AR> gather{(const typename AR::V*)p.v, l2_keep_policy()};
   Norms<AR> nm;
   nm.init();
-  for (int64_t s0 = gw * G; s0 < d.S; s0 += nw * G) {
-    const int64_t s = s0 + g;
-    const bool st_ok = s < d.S;
-    Cand<AR> run;
-    run.q = AR::inf(); run.q2 = AR::inf(); run.a = 0x7fffffff;
-    Qt qref = AR::inf();
-    const int aref = (p.pi_ref && st_ok) ? p.pi_ref[s] : -1;
-    for (int pass = 0; pass < npass; ++pass) {
-      const int a_local = pass * RPI + rr;
-      const bool act = st_ok && a_local < R;
-      const int a = act ? (p.pi_in ? p.pi_in[s] : a_local) : 0;
-      typename AR::Acc acc;
-      acc.init();
-      if (act) {
-        const int64_t base = ((int64_t)s * d.A + a) * d.kp;
-        for (int q0 = tl; q0 < nvec; q0 += 2 * T) {
-          Vec4<PT> pv[2];
-          int4 c4[2];
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            const int q = q0 + b * T;
-            if (q < nvec) {
-              pv[b].load(val + base + 4 * q);
-              c4[b] = __ldcs(reinterpret_cast<const int4*>(col + base) + q);
-            } else {
-              c4[b] = make_int4(0, 0, 0, 0);
-#pragma unroll
-              for (int e = 0; e < 4; ++e) pv[b].e[e] = PT(0);
-            }
-          }
-          V x[8];
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-            x[4 * b + 0] = ld_keep(v + c4[b].x, pol);
-            x[4 * b + 1] = ld_keep(v + c4[b].y, pol);
-            x[4 * b + 2] = ld_keep(v + c4[b].z, pol);
-            x[4 * b + 3] = ld_keep(v + c4[b].w, pol);
-          }
-#pragma unroll
-          for (int b = 0; b < 2; ++b) {
-#pragma unroll
-            for (int e = 0; e < 4; ++e) acc.add(pv[b].e[e], x[4 * b + e]);
-          }
-          acc.tick2();
-        }
-      }
-      const Qt sum = AR::reduce_team(acc.result(), T);
-      const Qt q = act ? AR::qval(d, s, a, sum) : AR::inf();
-      const bool allowed = act && (p.pi_in ? true : (d.mask ? d.mask[s * d.A + a] != 0 : true));
-      // reference-policy row of this pass (when it lies here): its lane holds qref.  Every
-      // lane takes part in the shuffle; only lanes whose reference row is in this pass keep it.
-      {
-        const int aoff = aref - pass * RPI;
-        const bool here = aref >= 0 && aoff >= 0 && aoff < Rp && aref < R;
-        const Qt qs = shfl_q<AR>(q, leader + (here ? aoff : 0) * T);
-        if (here) qref = qs;
-      }
-      Cand<AR> c;
-      c.q = allowed ? q : AR::inf();
-      c.q2 = AR::inf();
-      c.a = allowed ? a : 0x7fffffff;
-      for (int off = T; off < Rp * T; off <<= 1) c = cand_merge<AR>(c, cand_shfl<AR>(c, off));
-      run = cand_merge<AR>(run, c);
-    }
-    if (lane == leader && st_ok) {
-      Pick<AR> pk;
-      pk.best = run.q;
-      pk.second = run.q2;
-      pk.abest = p.pi_in ? p.pi_in[s] : (run.a == 0x7fffffff ? -1 : run.a);
-      pk.qref = qref;
-      emit_state<AR>(p, s, pk, nm);
+  if constexpr (QUEUE) {
+    EmitQueue<AR> eq;
+    eq.init();
+    for (int64_t s0 = gw * L.G; s0 < p.d.S; s0 += nw * L.G)
+      eq.push(p, L, s0, ell_state_group<PT, AR, T>(p, L, s0, gather), nm);
+    eq.flush(p, nm);
+  } else {
+    for (int64_t s0 = gw * L.G; s0 < p.d.S; s0 += nw * L.G) {
+      const Pick<AR> pk = ell_state_group<PT, AR, T>(p, L, s0, gather);
+      const int64_t s = s0 + L.g;
+      if (lane == L.leader && s < p.d.S) emit_state<AR>(p, s, pk, nm);
     }
   }
   finish_norms<AR>(p, nm, gp);
 }
 
-template <class PT, class AR, int T>
+template <class PT, class AR, int T, bool QUEUE>
 __global__ void __launch_bounds__(256, 3) sweep_ell_warp_kernel(SweepK p) {
-  sweep_ell_body<PT, AR, T>(p, this_grid());
+  sweep_ell_body<PT, AR, T, QUEUE>(p, this_grid());
+}
+
+// ------------------------------------------------------------------ ELL, banded columns
+// When every column lies within d.span states of its row's state, a block walks a contiguous
+// range of states in steps of WIN_NB, keeping v over [step - span, step + WIN_NB + span) in a
+// shared-memory ring that cp.async refills one step ahead.  The gathers then cost a few
+// shared-memory wavefronts instead of one L1 tag lookup per distinct line (a warp's 32 random
+// columns within +-span touch ~30 lines, which bounds the global-gather kernel).
+constexpr int WIN_RING = 4096;  // entries of v per block (8 bytes each)
+constexpr int WIN_NB = 256;     // states per step; span <= (WIN_RING - 2 WIN_NB) / 2
+constexpr int64_t WIN_SPAN_MAX = (WIN_RING - 2 * WIN_NB) / 2;
+
+__device__ __forceinline__ void win_cp8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_addr(smem)), "l"(gmem) : "memory");
+}
+
+template <class PT, class AR, int T>
+__global__ void __launch_bounds__(256, 4) sweep_ell_window_kernel(SweepK p, int64_t steps_per_block) {
+  using V = typename AR::V;
+  static_assert(sizeof(V) == 8, "window entries are 8 bytes");
+  __shared__ V ring[WIN_RING];
+  const DevMDP& d = p.d;
+  const EllLanes L = ell_lanes<T>(p);
+  const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const int64_t span = d.span;
+  const int64_t nsteps = (d.S + WIN_NB - 1) / WIN_NB;
+  const int64_t st0 = (int64_t)blockIdx.x * steps_per_block;
+  const int64_t st1 = min(nsteps, st0 + steps_per_block);
+  const V* v = (const V*)p.v;
+  auto fill = [&](int64_t x0, int64_t x1) {  // v[x], x in [x0, x1) and in [0, S), one group
+    const int64_t a0 = max(x0, (int64_t)0), a1 = min(x1, d.S);
+    for (int64_t x = a0 + threadIdx.x; x < a1; x += blockDim.x) win_cp8(ring + (x & (WIN_RING - 1)), v + x);
+    asm volatile("cp.async.commit_group;" ::: "memory");
+  };
+  const GatherRing<AR> gather{ring, WIN_RING - 1};
+  Norms<AR> nm;
+  nm.init();
+  EmitQueue<AR> eq;
+  eq.init();
+  if (st0 < st1) {
+    const int64_t lo = st0 * WIN_NB;
+    fill(lo - span, lo + WIN_NB + span);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");
+    __syncthreads();
+    for (int64_t stp = st0; stp < st1; ++stp) {
+      const int64_t s_lo = stp * WIN_NB, s_hi = s_lo + WIN_NB;
+      // the next step's new entries go where entries below s_lo - span were (the ring holds
+      // 2 WIN_NB + 2 span entries, so they never overwrite this step's window)
+      if (stp + 1 < st1) fill(s_hi + span, s_hi + WIN_NB + span);
+      for (int64_t s0 = s_lo + warp * L.G; s0 < s_hi && s0 < d.S; s0 += nwarp * L.G)
+        eq.push(p, L, s0, ell_state_group<PT, AR, T>(p, L, s0, gather), nm);
+      asm volatile("cp.async.wait_group 0;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  eq.flush(p, nm);
+  finish_norms<AR>(p, nm, this_grid());
 }
 
 // Batched sweep: the virtual blocks of every instance whose sweep is due.  The instance
@@ -819,10 +982,10 @@ __global__ void __launch_bounds__(256, 3) batch_sweep_kernel(BatchDev B) {
     }
     __syncthreads();
     switch (si.cls_sw) {
-      case 0: sweep_ell_body<float, ArDF, 1>(sp, gp); break;
-      case 1: sweep_ell_body<float, ArDF, 2>(sp, gp); break;
-      case 2: sweep_ell_body<float, ArDF, 4>(sp, gp); break;
-      default: sweep_ell_body<float, ArDF, 8>(sp, gp); break;
+      case 0: sweep_ell_body<float, ArDF, 1, false>(sp, gp); break;
+      case 1: sweep_ell_body<float, ArDF, 2, false>(sp, gp); break;
+      case 2: sweep_ell_body<float, ArDF, 4, false>(sp, gp); break;
+      default: sweep_ell_body<float, ArDF, 8, false>(sp, gp); break;
     }
   });
 }
@@ -878,21 +1041,45 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
     k<<<grid, 256, 0, st>>>(p);
   } else {
     const int T = L.lanes > 0 ? L.lanes : ell_sweep_lanes_default(d);
+    if (d.span >= 0 && d.span <= WIN_SPAN_MAX && !L.no_window && d.S >= 4 * WIN_NB) {
+      // banded columns: shared-memory window of v (block-contiguous steps of WIN_NB states)
+      const int64_t nsteps = (d.S + WIN_NB - 1) / WIN_NB;
+      int64_t blocks = L.grid > 0 ? L.grid : (int64_t)num_sms() * 4;
+      blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, nsteps));
+      blocks = std::min<int64_t>(blocks, MAX_RED_BLOCKS);
+      const int64_t spb = (nsteps + blocks - 1) / blocks;
+      const int grid = (int)((nsteps + spb - 1) / spb);
+      switch (T) {
+        case 1: sweep_ell_window_kernel<PT, AR, 1><<<grid, 256, 0, st>>>(p, spb); break;
+        case 2: sweep_ell_window_kernel<PT, AR, 2><<<grid, 256, 0, st>>>(p, spb); break;
+        case 4: sweep_ell_window_kernel<PT, AR, 4><<<grid, 256, 0, st>>>(p, spb); break;
+        case 8: sweep_ell_window_kernel<PT, AR, 8><<<grid, 256, 0, st>>>(p, spb); break;
+        default: return MDP_EINVAL;
+      }
+      return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+    }
     const int64_t units = (d.S + 7) / 8;
-    int grid = 1;
+    // a geometry fixed by the caller reproduces the batched kernel's grouping of the norm
+    // partial sums as well (outputs from the group leaders, no emit queue)
+    if (L.grid > 0) {
+      switch (T) {
+        case 1: sweep_ell_warp_kernel<PT, AR, 1, false><<<L.grid, 256, 0, st>>>(p); break;
+        case 2: sweep_ell_warp_kernel<PT, AR, 2, false><<<L.grid, 256, 0, st>>>(p); break;
+        case 4: sweep_ell_warp_kernel<PT, AR, 4, false><<<L.grid, 256, 0, st>>>(p); break;
+        case 8: sweep_ell_warp_kernel<PT, AR, 8, false><<<L.grid, 256, 0, st>>>(p); break;
+        default: return MDP_EINVAL;
+      }
+      return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
+    }
     switch (T) {
-      case 1: { auto k = sweep_ell_warp_kernel<PT, AR, 1>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
-        k<<<grid, 256, 0, st>>>(p); break; }
-      case 2: { auto k = sweep_ell_warp_kernel<PT, AR, 2>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
-        k<<<grid, 256, 0, st>>>(p); break; }
-      case 4: { auto k = sweep_ell_warp_kernel<PT, AR, 4>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
-        k<<<grid, 256, 0, st>>>(p); break; }
-      case 8: { auto k = sweep_ell_warp_kernel<PT, AR, 8>;
-        grid = L.grid > 0 ? L.grid : grid_for(k, 256, 0, units);
-        k<<<grid, 256, 0, st>>>(p); break; }
+      case 1: { auto k = sweep_ell_warp_kernel<PT, AR, 1, true>;
+        k<<<grid_for(k, 256, 0, units), 256, 0, st>>>(p); break; }
+      case 2: { auto k = sweep_ell_warp_kernel<PT, AR, 2, true>;
+        k<<<grid_for(k, 256, 0, units), 256, 0, st>>>(p); break; }
+      case 4: { auto k = sweep_ell_warp_kernel<PT, AR, 4, true>;
+        k<<<grid_for(k, 256, 0, units), 256, 0, st>>>(p); break; }
+      case 8: { auto k = sweep_ell_warp_kernel<PT, AR, 8, true>;
+        k<<<grid_for(k, 256, 0, units), 256, 0, st>>>(p); break; }
       default: return MDP_EINVAL;
     }
   }

@@ -405,3 +405,44 @@ def test_config3_full_size_sampled(mg):
         if two[1] - two[0] > 1e-6:
             assert pi[s] == int(np.argmin(q))
     h.close()
+
+
+# ------------------------------------------------------------------ banded data: windowed sweep
+# Columns within d.span of their state select the sweep that keeps a window of v in shared
+# memory (spans up to 1792 states); the last case's span exceeds it and takes the global-gather
+# sweep.  S spans one to many 256-state steps with ragged ends.
+@pytest.mark.parametrize("S,hw,shift", [(1024, 8, 2), (1500, 100, 20), (4100, 512, 64),
+                                        (16500, 1000, 100), (9000, 1700, 10), (9000, 1800, 10)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_bellman_banded_window_parity(mg, S, hw, shift, prec):
+    syn = mdp_synth.ell_banded(S, 6, 8, hw, shift, 0.99, seed=S + hw,
+                               val_dtype=np.float32 if prec == "mixed" else np.float64)
+    m = oracle.from_synth(syn)
+    h = mg.from_synth(syn)
+    rng = np.random.default_rng(S)
+    for trial in range(2):
+        v = rng.normal(size=S) * (10.0 if trial else 1.0) + 3.0 * trial
+        sw = oracle.bellman(m, v)
+        Tv, pi, res = mg.bellman_apply(h, v, precision=prec)
+        tol = 1e-13 if prec == "fp64" else 1e-12
+        assert rel_err(Tv, sw.Tv) <= tol
+        assert abs(res - sw.res_inf) <= tol * max(1.0, np.max(np.abs(sw.Tv)))
+        check_policy(pi, sw)
+    h.close()
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_windowed_and_global_sweeps_solve_alike(mg, prec):
+    """The windowed sweep gathers the same v values as the global one, so per-state outputs
+    agree bit for bit; only the grid's partial sums of ||Phi||_2 are grouped differently."""
+    syn = mdp_synth.ell_banded(6000, 16, 32, 512, 64, 0.999, seed=1003,
+                               val_dtype=np.float32 if prec == "mixed" else np.float64)
+    h = mg.from_synth(syn)
+    tol = 1e-9 if prec == "mixed" else 1e-11
+    v1, pi1, st1 = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec))
+    v2, pi2, st2 = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec, flags=mg.MDP_FLAG_NO_WINDOW))
+    assert st1["status"] == 0 and st2["status"] == 0
+    assert st1["outer"] == st2["outer"]
+    assert rel_err(v1, v2) <= (1e-7 if prec == "mixed" else 1e-11)
+    np.testing.assert_array_equal(pi1, pi2)
+    h.close()
