@@ -244,79 +244,98 @@ __global__ void __launch_bounds__(32) coarse_lu_kernel(float* band, int nc, int 
   cp_async_wait0();
 }
 
+// Reciprocal without branches: the approximate hardware reciprocal and one Newton step
+// (x' = x + x (1 - u x)), within an ulp or two, which is all the coarse factors need.
+__device__ __forceinline__ float rcp_nr(float u) {
+  float x;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(u));
+  return fmaf(x, fmaf(-u, x, 1.f), x);
+}
+
 // Single-thread banded LU for a narrow band (bw = BW <= 8), same elimination (GTH form) as
-// coarse_lu_kernel: the trailing window (rows k..k+BW, columns k..k+2BW) lives in registers, so
-// a pivot is a few dozen FP32 operations with no barrier; rows enter from a shared-memory ring
-// that cp.async fills LU1_AHEAD rows ahead.
+// coarse_lu_kernel.  Rows k..k+BW stay in registers in band form (slot i mod R holds row i:
+// b[slot][t] = A[i][i - BW + t]), so advancing the pivot moves no data: the pivot loop is
+// unrolled by R = BW + 1 and every slot index is static.  A finished row leaves in one
+// contiguous store; the next row enters its slot from a shared-memory ring that cp.async fills
+// LU1_AHEAD rows ahead.  The main loop has no branches (the scheduler interleaves the
+// independent row updates of consecutive pivots); the last pivots run with range guards.
 constexpr int LU1_AHEAD = 8;
+
+template <int BW, bool GUARD>
+__device__ __forceinline__ void lu1_pivot(float (&b)[BW + 1][2 * BW + 1], float (&sr)[BW + 1],
+                                          float (&orr)[BW + 1], float (*ring)[2 * BW + 3], int j,
+                                          int k, int nc, float* band) {
+  constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
+  const float u = sr[j] + orr[j];
+  const float rcp = rcp_nr(u);
+  b[j][BW] = u;
+#pragma unroll
+  for (int r = 1; r <= BW; ++r) {
+    const int q = (j + r) % R;  // static after unrolling
+    if (!GUARD || k + r < nc) {
+      const float sik = b[q][BW - r];  // S_{k+r,k} <= 0
+      const float l = sik * rcp;
+      b[q][BW - r] = l;
+      sr[q] = fmaf(-l, sr[j], sr[q]);
+      orr[q] = fmaxf(0.f, (orr[q] + sik) - l * (orr[j] + b[j][BW + r]));
+#pragma unroll
+      for (int c = 1; c <= BW; ++c)
+        if (c != r) b[q][c - r + BW] = fmaf(-l, b[j][BW + c], b[q][c - r + BW]);
+    }
+  }
+  float* rowk = band + (int64_t)k * Wp;
+#pragma unroll
+  for (int t = 0; t < W; ++t) rowk[t] = b[j][t];
+  const int i = k + R;  // the row entering slot j
+  if (!GUARD || i < nc) {
+    cp_async_wait_ahead();  // row i's group (the oldest pending) is complete
+    const float* src = ring[(i - R) % NS];
+#pragma unroll
+    for (int t = 0; t < W; ++t) b[j][t] = src[t];
+    sr[j] = src[W];
+    orr[j] = src[W + 1];
+    const int in = i + LU1_AHEAD;  // into the slot read one pivot ago
+    if (!GUARD || in < nc) {
+      float* dst = ring[(in - R) % NS];
+#pragma unroll
+      for (int t = 0; t < Wp; ++t) cp_async4(dst + t, band + (int64_t)in * Wp + t);
+    }
+    cp_async_commit();
+  }
+}
+
 template <int BW>
 __global__ void __launch_bounds__(1) coarse_lu1_kernel(float* band, int nc) {
   constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
   __shared__ float ring[NS][Wp];
-  float a[R][W];  // a[r][c]: Schur-complement entry (k + r, k + c)
-  float s[R], o[R];
-  auto issue = [&](int i) {  // row i into its ring slot (one commit group, maybe empty)
-    if (i < nc) {
-      float* dst = ring[(i - R) % NS];
-#pragma unroll
-      for (int t = 0; t < Wp; ++t) cp_async4(dst + t, band + (int64_t)i * Wp + t);
-    }
-    cp_async_commit();
-  };
+  float b[R][W];
+  float sr[R], orr[R];  // row sum and off-diagonal magnitude sum of each slot's row
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const bool in = r < nc;
 #pragma unroll
-    for (int c = 0; c < W; ++c) {
-      const int t = c - r + BW;  // row r holds columns r-BW .. r+BW
-      a[r][c] = (in && t >= 0 && t < W) ? band[(int64_t)r * Wp + t] : 0.f;
-    }
-    s[r] = in ? band[(int64_t)r * Wp + W] : 1.f;
-    o[r] = in ? band[(int64_t)r * Wp + W + 1] : 0.f;
+    for (int t = 0; t < W; ++t) b[r][t] = in ? band[(int64_t)r * Wp + t] : 0.f;
+    sr[r] = in ? band[(int64_t)r * Wp + W] : 1.f;
+    orr[r] = in ? band[(int64_t)r * Wp + W + 1] : 0.f;
   }
-  for (int q = 0; q < LU1_AHEAD; ++q) issue(R + q);
-  for (int k = 0; k < nc; ++k) {
-    const float u = s[0] + o[0];
-    const float rcp = 1.f / u;
-    float* rowk = band + (int64_t)k * Wp;
-    rowk[BW] = u;
-#pragma unroll
-    for (int c = 1; c <= BW; ++c) rowk[BW + c] = a[0][c];
-#pragma unroll
-    for (int r = 1; r <= BW; ++r) {
-      if (k + r < nc) {
-        const float l = a[r][0] * rcp;
-        band[(int64_t)(k + r) * Wp + BW - r] = l;
-        s[r] = fmaf(-l, s[0], s[r]);
-        o[r] = fmaxf(0.f, (o[r] + a[r][0]) - l * (o[0] + a[0][r]));
-#pragma unroll
-        for (int c = 1; c <= BW; ++c)
-          if (c != r) a[r][c] = fmaf(-l, a[0][c], a[r][c]);
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < BW; ++r) {
-#pragma unroll
-      for (int c = 0; c < W - 1; ++c) a[r][c] = a[r + 1][c + 1];
-      a[r][W - 1] = 0.f;
-      s[r] = s[r + 1];
-      o[r] = o[r + 1];
-    }
-    const int i = k + 1 + BW;  // the row entering the window
+  for (int q = 0; q < LU1_AHEAD; ++q) {
+    const int i = R + q;
     if (i < nc) {
-      cp_async_wait_ahead();   // row i's group (the oldest pending) is complete
-      const float* src = ring[(i - R) % NS];
 #pragma unroll
-      for (int c = 0; c < W; ++c) a[BW][c] = src[c];
-      s[BW] = src[W];
-      o[BW] = src[W + 1];
-      issue(i + LU1_AHEAD);    // into the slot read one pivot ago
-    } else {
-#pragma unroll
-      for (int c = 0; c < W; ++c) a[BW][c] = 0.f;
-      s[BW] = 1.f;
-      o[BW] = 0.f;
+      for (int t = 0; t < Wp; ++t) cp_async4(&ring[(i - R) % NS][t], band + (int64_t)i * Wp + t);
     }
+    cp_async_commit();
+  }
+  int k0 = 0;
+  // every row a pivot of this round touches exists, and so does every row it prefetches
+  for (; k0 + 2 * R + LU1_AHEAD + BW <= nc; k0 += R) {
+#pragma unroll
+    for (int j = 0; j < R; ++j) lu1_pivot<BW, false>(b, sr, orr, ring, j, k0 + j, nc, band);
+  }
+  for (; k0 < nc; k0 += R) {
+#pragma unroll
+    for (int j = 0; j < R; ++j)
+      if (k0 + j < nc) lu1_pivot<BW, true>(b, sr, orr, ring, j, k0 + j, nc, band);
   }
   cp_async_wait0();
 }
