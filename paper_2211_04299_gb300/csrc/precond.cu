@@ -386,9 +386,21 @@ __global__ void __launch_bounds__(32) coarse_inverse_kernel(const float* cl, con
       for (int64_t e = lane; e < nc; e += 32) csm[(int64_t)nc * RW + e] = dinv[e];
     __syncwarp();
   };
-  auto coef = [&](const float* g, int64_t k, int q) -> float {
-    if constexpr (STAGED) return csm[k * RW + q];
-    else return __ldg(g + k * 32 + q);
+  // the RW coefficients of step k as vector loads (rows are 16-byte aligned for RW >= 4)
+  auto coefs = [&](const float* g, int64_t k, float (&c)[RW]) {
+    const float* src = STAGED ? csm + k * RW : g + k * 32;
+    if constexpr (RW >= 4) {
+#pragma unroll
+      for (int i = 0; i < RW / 4; ++i) {
+        const float4 v = STAGED ? reinterpret_cast<const float4*>(src)[i]
+                                : __ldg(reinterpret_cast<const float4*>(src) + i);
+        c[4 * i] = v.x; c[4 * i + 1] = v.y; c[4 * i + 2] = v.z; c[4 * i + 3] = v.w;
+      }
+    } else {
+      const float2 v = STAGED ? *reinterpret_cast<const float2*>(src)
+                              : __ldg(reinterpret_cast<const float2*>(src));
+      c[0] = v.x; c[1] = v.y;
+    }
   };
   auto dk = [&](int64_t k) -> float {
     if constexpr (STAGED) return csm[(int64_t)nc * RW + k];
@@ -398,21 +410,26 @@ __global__ void __launch_bounds__(32) coarse_inverse_kernel(const float* cl, con
   float h[RW];
 #pragma unroll
   for (int q = 0; q < RW; ++q) h[q] = 0.f;
-  // forward: k = j0 .. nc-1 (y[k] = 0 below the warp's first column)
-  for (int64_t kb = j0; kb < nc; kb += 32) {
+  // forward: k = j0 .. nc-1 (y[k] = 0 below the warp's first column); full blocks of 32
+  // steps have no branches, so the scheduler overlaps consecutive steps' older terms
+  auto fstep = [&](int s, int64_t k) {
+    float c[RW];
+    coefs(cl, k, c);
+    float part = (k == j) ? 1.f : 0.f;
 #pragma unroll
-    for (int s = 0; s < 32; ++s) {
-      const int64_t k = kb + s;
-      if (k < nc) {
-        float part = (k == j) ? 1.f : 0.f;
+    for (int q = 1; q < RW; ++q) part = fmaf(c[q], h[(s - 1 - q) & (RW - 1)], part);
+    const float y = fmaf(c[0], h[(s - 1) & (RW - 1)], part);
+    h[s & (RW - 1)] = y;
+    if (own) inv[k * ldi + j] = y;
+  };
+  int64_t kb = j0;
+  for (; kb + 32 <= nc; kb += 32) {
 #pragma unroll
-        for (int q = 1; q < RW; ++q) part = fmaf(coef(cl, k, q), h[(s - 1 - q) & (RW - 1)], part);
-        const float y = fmaf(coef(cl, k, 0), h[(s - 1) & (RW - 1)], part);
-        h[s & (RW - 1)] = y;
-        if (own) inv[k * ldi + j] = y;
-      }
-    }
+    for (int s = 0; s < 32; ++s) fstep(s, kb + s);
   }
+#pragma unroll
+  for (int s = 0; s < 32; ++s)
+    if (kb + s < nc) fstep(s, kb + s);
   if constexpr (STAGED) stage(cu, true);
   __syncwarp();
 #pragma unroll
@@ -426,25 +443,29 @@ __global__ void __launch_bounds__(32) coarse_inverse_kernel(const float* cl, con
       dst[s] = (k >= j0 && own) ? inv[k * ldi + j] : 0.f;
     }
   };
+  auto bstep = [&](int s, int64_t k) {
+    float c[RW];
+    coefs(cu, k, c);
+    float part = yb[s] * dk(k);
+#pragma unroll
+    for (int q = 1; q < RW; ++q) part = fmaf(c[q], h[(s - 1 - q) & (RW - 1)], part);
+    const float x = fmaf(c[0], h[(s - 1) & (RW - 1)], part);
+    h[s & (RW - 1)] = x;
+    if (own) inv[k * ldi + j] = x;
+  };
   load_y(nc - 1, yb);
-  for (int64_t kb = nc - 1; kb >= 0; kb -= 32) {
+  int64_t kd = nc - 1;
+  for (; kd - 31 >= 0; kd -= 32) {
     float yn[32];
-    load_y(kb - 32, yn);  // the next block, in flight while this one runs
+    load_y(kd - 32, yn);  // the next block, in flight while this one runs
 #pragma unroll
-    for (int s = 0; s < 32; ++s) {
-      const int64_t k = kb - s;
-      if (k >= 0) {
-        float part = yb[s] * dk(k);
-#pragma unroll
-        for (int q = 1; q < RW; ++q) part = fmaf(coef(cu, k, q), h[(s - 1 - q) & (RW - 1)], part);
-        const float x = fmaf(coef(cu, k, 0), h[(s - 1) & (RW - 1)], part);
-        h[s & (RW - 1)] = x;
-        if (own) inv[k * ldi + j] = x;
-      }
-    }
+    for (int s = 0; s < 32; ++s) bstep(s, kd - s);
 #pragma unroll
     for (int s = 0; s < 32; ++s) yb[s] = yn[s];
   }
+#pragma unroll
+  for (int s = 0; s < 32; ++s)
+    if (kd - s >= 0) bstep(s, kd - s);
 }
 
 // Arnoldi step (mode STEP): Q_i = x * scale (x = start residual or previous w) and its block

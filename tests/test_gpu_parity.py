@@ -446,3 +446,28 @@ def test_windowed_and_global_sweeps_solve_alike(mg, prec):
     assert rel_err(v1, v2) <= (1e-7 if prec == "mixed" else 1e-11)
     np.testing.assert_array_equal(pi1, pi2)
     h.close()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_policy_sweeps_on_banded_data(mg, prec):
+    """Policy sweeps (T^pi v, one row per state) also take the windowed kernel on banded data:
+    OPI, Alg. 1 with VI inner steps and GMRES policy evaluation against the oracle."""
+    syn = mdp_synth.ell_banded(5000, 8, 16, 300, 40, 0.95, seed=77,
+                               val_dtype=np.float32 if prec == "mixed" else np.float64)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-12)
+    h = mg.from_synth(syn)
+    tol = 1e-8 if prec == "mixed" else 1e-11
+    bound = 1e-6 if prec == "mixed" else 1e-9
+    for solve in (mg.opi_solve, mg.ipi_vi_solve):
+        v, pi, st = solve(h, mg.opts(tol=tol, precision=prec, opi_W=20, max_outer=2000))
+        assert st["status"] == 0, (solve.__name__, st)
+        assert rel_err(v, ref.v) <= bound
+    pi0 = np.asarray(ref.pi, dtype=np.int32)
+    ve, ste = mg.policy_eval_gmres(h, pi0, target_inf=1e-10, o=mg.opts(precision=prec))
+    if prec == "fp64":
+        assert ste["status"] == 0
+        assert rel_err(ve, oracle.policy_evaluation(m, pi0)) <= 1e-10
+    else:
+        assert rel_err(ve, oracle.policy_evaluation(m, pi0)) <= 1e-6
+    h.close()
