@@ -119,6 +119,27 @@ def source_hash():
     return h.hexdigest()[:16]
 
 
+WIN_SPAN_MAX, WIN_MIN_S = 1792, 1024  # the library's windowed-sweep rule (banded ELL data)
+
+
+def sweep_kernel_name(syn):
+    """The sweep kernel the library runs for this MDP (same rule as the library's launcher)."""
+    if syn.kind == "dense":
+        return "sweep_dense_tma_kernel"
+    rows = np.arange(syn.S, dtype=np.int32)[:, None]
+    span = max(int(np.max(np.abs(syn.col[a] - rows))) for a in range(syn.A))
+    return ("sweep_ell_window_kernel" if span <= WIN_SPAN_MAX and syn.S >= WIN_MIN_S
+            else "sweep_ell_warp_kernel")
+
+
+def sweep_traffic(args, syn):
+    if syn.kind == "dense" and syn.S == S_:
+        return traffic_for("sweep_dense_df_cfg2")
+    if args.config == 3 and syn.S == 1_000_000:
+        return traffic_for("sweep_ell_window_cfg3")
+    return None
+
+
 def traffic_for(kernel_key):
     """DRAM bytes per launch from the committed ncu summary, if it was taken on the current
     kernel source; otherwise None."""
@@ -864,10 +885,10 @@ def main():
                       if mvs else {"ms": None, "algorithmic_bytes": mb,
                                    "note": "launched inside the CUDA graph of the inner loop"}),
         "roofline": {"bound": "hbm",
-                     "kernel": "sweep_dense_tma_kernel" if syn.kind == "dense" else "sweep_ell_kernel",
+                     "kernel": sweep_kernel_name(syn),
                      "achieved": sweep_gbs, "peak": peak, "unit": "GB/s",
                      "frac": sweep_gbs / peak, "peak_source": peak_kind,
-                     "traffic": traffic_for("sweep_dense_df_cfg2") if (syn.kind == "dense" and S == S_) else None},
+                     "traffic": sweep_traffic(args, syn)},
         "gpu_launches": launches,
         "clocks": clk,
     }
