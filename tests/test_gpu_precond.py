@@ -167,3 +167,39 @@ def test_precond_config3_full_size_sampled(mg):
     _, _, st0 = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed"))
     assert st["inner"] * 4 <= st0["inner"], (st["inner"], st0["inner"])
     h.close()
+
+
+@pytest.mark.parametrize("W", [2, 3])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_precond_with_restarts_matches_oracle(mg, W, prec):
+    """Short restart cycles (W = 2, 3) make inner solves restart from the candidate
+    V_k + M^{-1} Q y, whose coarse part the combine kernel forms in RESTART mode."""
+    syn = banded(3000, prec, seed=5, halfwidth=200, shift=40)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-11)
+    refp = oracle.gmres_policy_iteration(m, alpha=0.1, W=W, tol=1e-10, precond_block=128)
+    assert refp.restarts > 0
+    h = mg.from_synth(syn)
+    tol = 1e-8 if prec == "mixed" else 1e-10
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec, restart=W, precond_block=128))
+    assert st["status"] == 0 and st["restarts"] > 0, st
+    assert rel_err(v, ref.v) <= (1e-6 if prec == "mixed" else 1e-8)
+    check_policy(pi, oracle.bellman(m, ref.v))
+    if prec == "fp64":
+        assert abs(st["outer"] - refp.outer) <= 2
+    h.close()
+
+
+def test_precond_inner_cap_reaches_the_same_fixed_point(mg):
+    """An inner step cap (FINISH mode forms the capped candidate with its coarse part) slows
+    the outer loop but not its fixed point."""
+    syn = banded(3000, "fp64", seed=5, halfwidth=200, shift=40)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-11)
+    h = mg.from_synth(syn)
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-10, precision="fp64", max_inner=2,
+                                        max_outer=500, precond_block=128))
+    assert st["status"] == 0, st
+    assert rel_err(v, ref.v) <= 1e-8
+    check_policy(pi, oracle.bellman(m, ref.v))
+    h.close()
