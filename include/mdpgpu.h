@@ -137,11 +137,11 @@ typedef struct {
  * MDP_FLAG_HOST_LOOP enqueues the same kernels step by step from the host instead (one
  * host wait per Arnoldi step), for tools that cannot follow conditional graph nodes. */
 #define MDP_FLAG_HOST_LOOP 1
-/* ELL data whose columns all lie within a few thousand states of their row's state (banded
- * P, measured when the data is validated) is swept by a kernel that keeps a window of v in
- * shared memory; MDP_FLAG_NO_WINDOW makes the solvers use the global-gather sweep instead
- * (same values; for comparison and profiling).  mdp_set_geometry with sweep_blocks > 0 also
- * selects the global-gather sweep. */
+/* ELL data whose columns all lie within 1792 states of their row's state (banded P, measured
+ * when the data is validated) is swept, and multiplied in the Arnoldi steps, by kernels that
+ * keep a window of the vector in shared memory; MDP_FLAG_NO_WINDOW makes the solvers use the
+ * global-gather kernels instead (same values; for comparison and profiling).  mdp_set_geometry
+ * with sweep_blocks > 0 (matvec_blocks > 0) also selects the global-gather sweep (matvec). */
 #define MDP_FLAG_NO_WINDOW 2
 
 /* alpha 0.1, tol 1e-8, restart 30, max_outer 100, max_inner 3000, precision MIXED,

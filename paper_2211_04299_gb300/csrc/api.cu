@@ -115,6 +115,7 @@ struct mdp_s {
   } pc;
   int pc_on = 0;           // the current solve applies the preconditioner
   int no_window = 0;       // the current solve asked for the global-gather ELL sweep
+  int64_t last_span = -2;  // column reach of the data the inner graphs were captured for
   // graph-resident inner GMRES loops of ipi_solve: [0] a fresh solve on Phi_k, [1] a solve
   // resumed on the exact residual found by the verifying sweep (rebuilt when parameters change)
   struct InnerGraph {
@@ -123,6 +124,7 @@ struct mdp_s {
     double alpha = -1.0, forcing_c = -1.0, thr_floor = -1.0;
     const void* ws = nullptr;
     const void* pcz = nullptr;  // preconditioner buffers the graph was captured with (or null)
+    int nowin = -1;             // MDP_FLAG_NO_WINDOW at capture (selects the matvec kernel)
   } ig[2];
   cudaStream_t cap = nullptr;
   std::vector<cudaEvent_t> ev;   // event pool (pairs)
@@ -534,6 +536,7 @@ int enqueue_step(mdp_t h, const int32_t* pi_dev, const void* rhs, cudaStream_t s
   M.err = w.flags + 8;
   M.lanes = h->lanes_matvec;
   M.grid = h->grid_matvec;
+  M.no_window = h->no_window;
   MatvecLaunch C = M;
   C.gate_mode = GM_CHECK;
   C.gate_mode2 = GM_RESTART;
@@ -646,6 +649,7 @@ int build_inner_graph(mdp_t h, int variant, const int32_t* pi_dev, double alpha,
   gg.thr_floor = h->thr_floor;
   gg.ws = w.ctl;
   gg.pcz = h->pc_on ? h->pc.z : nullptr;
+  gg.nowin = h->no_window;
   return MDP_OK;
 }
 
@@ -655,7 +659,7 @@ int launch_inner_graph(mdp_t h, int variant, double alpha, int W, int max_steps)
   auto& gg = h->ig[variant];
   if (!gg.exec || gg.kt != w.kt || gg.W != W || gg.steps != max_steps || gg.alpha != alpha ||
       gg.forcing_c != h->forcing_c || gg.thr_floor != h->thr_floor ||
-      gg.ws != w.ctl || gg.pcz != (h->pc_on ? h->pc.z : nullptr))
+      gg.ws != w.ctl || gg.pcz != (h->pc_on ? h->pc.z : nullptr) || gg.nowin != h->no_window)
     RK(build_inner_graph(h, variant, w.pi, alpha, W, max_steps));
   CK(cudaGraphLaunch(gg.exec, h->stream));
   return MDP_OK;
@@ -951,7 +955,17 @@ int finish_upload(mdp_t h) {
   if (hf[2]) return fail(MDP_EINVAL, "a transition row does not sum to 1 within tolerance");
   if (hf[3]) return fail(MDP_EINVAL, "costs must be finite");
   if (hf[4]) return fail(MDP_EINVAL, "every state needs at least one allowed action");
-  h->d.span = h->d.kind == KIND_ELL ? hf[6] : -1;  // column reach: banded data sweeps windowed
+  const int64_t span = h->d.kind == KIND_ELL ? hf[6] : -1;  // column reach: banded data windowed
+  if (span != h->last_span) {
+    // inner-loop graphs hold the DevMDP (and so the kernel choice) they were captured with
+    for (auto& gg : h->ig)
+      if (gg.exec) {
+        cudaGraphExecDestroy(gg.exec);
+        gg.exec = nullptr;
+      }
+    h->last_span = span;
+  }
+  h->d.span = span;
   return MDP_OK;
 }
 

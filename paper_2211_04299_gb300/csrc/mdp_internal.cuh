@@ -442,6 +442,7 @@ struct MatvecLaunch {
   int no_tma;
   const void* x_pre;    // gate STEP with a preconditioner: multiply this vector (M^{-1} Q_i,
                         // already formed) with scale 1 and leave Q_i alone
+  int no_window;        // ELL: force the global-gather kernel even for banded columns
 };
 
 int launch_matvec(const MatvecLaunch& L, cudaStream_t st);

@@ -471,3 +471,21 @@ def test_policy_sweeps_on_banded_data(mg, prec):
     else:
         assert rel_err(ve, oracle.policy_evaluation(m, pi0)) <= 1e-6
     h.close()
+
+
+def test_reload_changes_the_window_choice(mg):
+    """A handle solved on banded data (windowed kernels, captured in the inner-loop graph) and
+    then reloaded with uniformly spread columns of the same shape must switch back to the
+    global-gather kernels: the solve of the new data matches the oracle."""
+    S, A, k = 3000, 6, 16
+    band = mdp_synth.ell_banded(S, A, k, 200, 30, 0.99, seed=11, val_dtype=np.float32)
+    unif = mdp_synth.ell_uniform(S, A, k, 0.99, seed=12, val_dtype=np.float32)
+    h = mg.from_synth(band)
+    for syn in (band, unif, band):
+        mg.mdp_load_ell(h, syn.col, syn.val, syn.g)
+        m = oracle.from_synth(syn)
+        ref = oracle.policy_iteration(m, tol=1e-11)
+        v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed"))
+        assert st["status"] == 0
+        assert rel_err(v, ref.v) <= 1e-6
+    h.close()
