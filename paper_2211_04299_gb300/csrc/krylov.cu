@@ -155,6 +155,7 @@ __device__ __forceinline__ void matvec_finish(const MatvecK& p, KT mx, KT ss,
   c->dsel = 1 - c->dsel;
   c->restarts += 1;
   c->beta = rn2;
+  c->est_ratio = rn2 > 0.0 ? rinf / rn2 : 1.0;
   for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
   c->gv[0] = rn2;
   c->i = 0;
@@ -824,7 +825,11 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
   } else if (c->steps >= c->max_steps) {
     mode = GM_FINISH;
     c->status = GS_CAP;
-  } else if (c->rho <= c->sqrtS * c->thr) {
+  } else if (c->rho <= c->sqrtS * c->thr &&
+             (c->rho * c->est_ratio <= 2.0 * c->thr || c->steps - c->est_last >= 4)) {
+    // ||r||_inf >= ||r||_2 / sqrt(S) rules the estimate out above sqrt(S) thr; below it, the
+    // pass over Q runs when rho times the last observed inf/2-norm ratio comes within 2x of
+    // the threshold, and at least every 4 steps (the ratio is a prediction, not a bound)
     mode = GM_EST;
   } else if (i >= c->W - 1) {
     mode = GM_RESTART;
@@ -985,6 +990,8 @@ __device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp)
     } else if (est) {
       c->est_runs += 1;
       c->last_inf = (double)t;
+      c->est_last = c->steps;
+      if (c->rho > 0.0) c->est_ratio = (double)t / c->rho;
       if (c->accept_est && (double)t <= c->thr) {
         // accepted on the estimate: the candidate is the result; the caller's next Bellman
         // sweep evaluates the exact residual of this policy and resumes the solve if needed

@@ -316,6 +316,8 @@ struct GmresCtl {
   double thr_saved; // threshold of the current outer iteration (kept for a resumed solve)
   int accept_est;   // accept on the Arnoldi-relation estimate (the caller verifies exactly)
   int resumed;
+  int est_last;     // steps at the last estimate pass
+  double est_ratio; // ||r||_inf / ||r||_2 last observed (start residual, estimate or restart)
   double H[(WMAX + 1) * WMAX];  // column-major, leading dimension WMAX+1
   double cs[WMAX], sn[WMAX];
   double gv[WMAX + 1];
@@ -377,6 +379,8 @@ __device__ inline void gmres_init_ctl(GmresCtl* c, double thr, double alpha, dou
   c->resumed = resume;
   const double beta = rhs->res_nrm2;
   c->beta = beta;
+  c->est_last = 0;
+  c->est_ratio = beta > 0.0 ? rhs->res_inf / beta : 1.0;
   for (int j = 0; j <= WMAX; ++j) c->gv[j] = 0.0;
   c->gv[0] = beta;
   gmres_set_scale(c, beta > 0.0 ? 1.0 / beta : 0.0);
