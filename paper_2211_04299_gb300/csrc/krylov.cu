@@ -651,6 +651,26 @@ template <> struct TSv<double> {
   static __device__ __forceinline__ double amax(V x) { return fmax(fabs(x.x), fabs(x.y)); }
 };
 
+// Vector-unit load, with an L2 evict-last hint when KEEP: the single-instance Krylov basis
+// (a few tens of MB at S = 10^6) then stays in L2 across Arnoldi steps while the matvec and
+// sweep streams (loaded evict-first) pass through.
+template <class KT, bool KEEP>
+__device__ __forceinline__ typename TSv<KT>::V tsld(uint64_t pol, const KT* p) {
+  if constexpr (!KEEP) {
+    return TSv<KT>::ld(p);
+  } else if constexpr (sizeof(KT) == 4) {
+    float4 r;
+    asm volatile("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
+                 : "=f"(r.x), "=f"(r.y), "=f"(r.z), "=f"(r.w) : "l"(p), "l"(pol));
+    return r;
+  } else {
+    double2 r;
+    asm volatile("ld.global.L2::cache_hint.v2.f64 {%0, %1}, [%2], %3;"
+                 : "=d"(r.x), "=d"(r.y) : "l"(p), "l"(pol));
+    return r;
+  }
+}
+
 // This block's range of vector units [u0, u1).
 template <class KT>
 __device__ __forceinline__ void block_units(int64_t S, int64_t& u0, int64_t& u1, GridPos gp) {
@@ -711,8 +731,9 @@ __device__ __forceinline__ void reduce_dots(const KT* part, int m, double* outd,
 // CGS2 pass 1: c1 = Q_{0..i}^T w.  Each thread keeps MAXM column accumulators (MAXM is
 // fixed by the restart length, so the loop is static) and streams its vector units of w and
 // of every Q_j once.
-template <class KT, int MAXM>
+template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void cgs_dots_body(const KB& b, GridPos gp) {
+  const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
@@ -725,14 +746,14 @@ __device__ __forceinline__ void cgs_dots_body(const KB& b, GridPos gp) {
 #pragma unroll
   for (int j = 0; j < MAXM; ++j) acc[j] = 0;
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    const typename T::V wv = T::ld(w + u * T::R);
+    const typename T::V wv = tsld<KT, KEEP>(pol, w + u * T::R);
 #pragma unroll
     for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
       if (j0 < m) {
         typename T::V q[TS_BATCH];
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t)
-          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t) acc[j0 + t] += T::dot(q[t], wv);
       }
@@ -745,8 +766,9 @@ __device__ __forceinline__ void cgs_dots_body(const KB& b, GridPos gp) {
 
 // CGS2 pass 1 update and pass 2 projection: w -= Q c1, then c2 = Q^T w.  The second read of
 // each Q_j unit follows the first within the same thread and is served by L1.
-template <class KT, int MAXM>
+template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void cgs_axpy_dots_body(const KB& b, GridPos gp) {
+  const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
@@ -761,14 +783,14 @@ __device__ __forceinline__ void cgs_axpy_dots_body(const KB& b, GridPos gp) {
 #pragma unroll
   for (int j = 0; j < MAXM; ++j) acc[j] = 0;
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    typename T::V wv = T::ld(w + u * T::R);
+    typename T::V wv = tsld<KT, KEEP>(pol, w + u * T::R);
 #pragma unroll
     for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
       if (j0 < m) {
         typename T::V q[TS_BATCH];
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t)
-          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t) wv = T::axpy(-cf[j0 + t], q[t], wv);
       }
@@ -780,7 +802,7 @@ __device__ __forceinline__ void cgs_axpy_dots_body(const KB& b, GridPos gp) {
         typename T::V q[TS_BATCH];
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t)
-          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t) acc[j0 + t] += T::dot(q[t], wv);
       }
@@ -866,8 +888,9 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
 }
 
 // CGS2 pass 2 update, ||w||_2 and the Givens step: w -= Q c2.
-template <class KT, int MAXM>
+template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void cgs_axpy_norm_body(const KB& b, GridPos gp) {
+  const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
@@ -880,14 +903,14 @@ __device__ __forceinline__ void cgs_axpy_norm_body(const KB& b, GridPos gp) {
   block_units<KT>(b.S, u0, u1, gp);
   KT ss = 0;
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    typename T::V wv = T::ld(w + u * T::R);
+    typename T::V wv = tsld<KT, KEEP>(pol, w + u * T::R);
 #pragma unroll
     for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
       if (j0 < m) {
         typename T::V q[TS_BATCH];
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t)
-          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t) wv = T::axpy(-cf[j0 + t], q[t], wv);
       }
@@ -932,8 +955,9 @@ __device__ __forceinline__ double2 add_coarse<double>(double2 x, double e, int64
 // candidate by the Arnoldi relation J Q_i = Q_{i+1} H (exact arithmetic).  The last block
 // decides: EST -> accept (or CHECK) when ||r||_inf meets the threshold, else the next step or
 // a restart; FINISH -> DONE with the candidate as the result.
-template <class KT, int MAXM>
+template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp) {
+  const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   const int mode = *(volatile int*)&c->mode;
@@ -955,15 +979,15 @@ __device__ __forceinline__ void estimate_candidate_body(const KB& b, GridPos gp)
   block_units<KT>(b.S, u0, u1, gp);
   KT mx = 0;
   for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    typename T::V x = T::ld(base + u * T::R);
-    typename T::V e = est ? T::axpy(zl, T::ld(w + u * T::R), T::zero()) : T::zero();
+    typename T::V x = tsld<KT, KEEP>(pol, base + u * T::R);
+    typename T::V e = est ? T::axpy(zl, tsld<KT, KEEP>(pol, w + u * T::R), T::zero()) : T::zero();
 #pragma unroll
     for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
       if (j0 < m) {
         typename T::V q[TS_BATCH];
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t)
-          q[t] = T::ld(Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
 #pragma unroll
         for (int t = 0; t < TS_BATCH; ++t) {
           x = T::axpy(cy[j0 + t], q[t], x);
@@ -1224,19 +1248,19 @@ int launch_matvec(const MatvecLaunch& L, cudaStream_t st) {
 
 template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) cgs_dots_kernel(KB b) {
-  cgs_dots_body<KT, MAXM>(b, this_grid());
+  cgs_dots_body<KT, MAXM, true>(b, this_grid());
 }
 template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_dots_kernel(KB b) {
-  cgs_axpy_dots_body<KT, MAXM>(b, this_grid());
+  cgs_axpy_dots_body<KT, MAXM, true>(b, this_grid());
 }
 template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) cgs_axpy_norm_kernel(KB b) {
-  cgs_axpy_norm_body<KT, MAXM>(b, this_grid());
+  cgs_axpy_norm_body<KT, MAXM, true>(b, this_grid());
 }
 template <class KT, int MAXM>
 __global__ void __launch_bounds__(RED_THREADS) estimate_candidate_kernel(KB b) {
-  estimate_candidate_body<KT, MAXM>(b, this_grid());
+  estimate_candidate_body<KT, MAXM, true>(b, this_grid());
 }
 
 // ------------------------------------------------------------------ batched kernels
