@@ -488,14 +488,24 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
             b2.tune()
         sets = [(hs, b), (hs2, b2)]
 
-        def e2e_run(k):
-            for hh, (c, v, g) in zip(sets[0][0], pins):
+        # issuing 256 handles' uploads is thousands of API calls: a second host thread issues
+        # the next set's while this one waits for the current batch (calls on different
+        # handles are independent; the library's error message is per thread)
+        from concurrent.futures import ThreadPoolExecutor
+        loader = ThreadPoolExecutor(max_workers=1)
+
+        def load_set(j):
+            torch.cuda.set_device(local)  # the loader thread works on this rank's GPU
+            for hh, (c, v, g) in zip(sets[j][0], pins):
                 mg.mdp_load_ell_async(hh, c, v, g)
+
+        def e2e_run(k):
+            load_set(0)
             for i in range(k):
-                if i + 1 < k:
-                    for hh, (c, v, g) in zip(sets[(i + 1) % 2][0], pins):
-                        mg.mdp_load_ell_async(hh, c, v, g)
+                nxt = loader.submit(load_set, (i + 1) % 2) if i + 1 < k else None
                 sets[i % 2][1].solve(vh, ph)
+                if nxt is not None:
+                    nxt.result()
 
         e2e_run(2)
         torch.cuda.synchronize()
@@ -505,6 +515,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
         e2e_run(e2e_steps)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
+        loader.shutdown()
         b2.close()
         for hh in hs2:
             hh.close()
