@@ -916,10 +916,10 @@ def main():
         torch.cuda.synchronize()
         return n / (b0.elapsed_time(b1) / 1000.0), stv
 
-    # the banded workload with the two-level preconditioned inner solve (blocks of 256
-    # states), for reference beside the plain Alg. 2 line
+    # the banded workload with the two-level preconditioned inner solve (blocks of 512
+    # states: measured best of 128..2048), for reference beside the plain Alg. 2 line
     if args.config == 3 and args.precond_block == 0:
-        pb = 256
+        pb = 512
         rate, stp = timed_variant(mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
                                           precond_block=pb), min(args.steps, 10))
         line["two_level_precond"] = {"precond_block": pb, "value": rate, "unit": "solves/s",
