@@ -848,10 +848,13 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
     mode = GM_FINISH;
     c->status = GS_CAP;
   } else if (c->rho <= c->sqrtS * c->thr &&
-             (c->rho * c->est_ratio <= 2.0 * c->thr || c->steps - c->est_last >= 4)) {
-    // ||r||_inf >= ||r||_2 / sqrt(S) rules the estimate out above sqrt(S) thr; below it, the
-    // pass over Q runs when rho times the last observed inf/2-norm ratio comes within 2x of
-    // the threshold, and at least every 4 steps (the ratio is a prediction, not a bound)
+             (c->sqrtS < 256.0 || c->rho * c->est_ratio <= 2.0 * c->thr ||
+              c->steps - c->est_last >= 4)) {
+    // ||r||_inf >= ||r||_2 / sqrt(S) rules the estimate out above sqrt(S) thr.  Below it, for
+    // S >= 65536 (where that band is wide and a pass over Q costs as much as a step), the pass
+    // runs when rho times the last observed inf/2-norm ratio comes within 2x of the threshold,
+    // and at least every 4 steps (the ratio is a prediction, not a bound); smaller problems
+    // estimate at every step of the band
     mode = GM_EST;
   } else if (i >= c->W - 1) {
     mode = GM_RESTART;
