@@ -59,7 +59,8 @@ __global__ void coarse_bandwidth_kernel(DevMDP d, int lb, int* bw) {
 // Row I of the coarse operator (one block per coarse row), stored as Wp = 2 bw + 3 floats:
 //   band[I][t], t = J - I + bw < W:  J_c[I][J] = delta_{IJ} - gamma / |I| * sum_{s in I} sum_{c in J} p(s, c)
 //   band[I][W]:      s_I = row sum of J_c = (1 - gamma) + gamma * mean_{s in I} (1 - sum_c p(s, c))
-//   band[I][W + 1]:  o_I = sum of |J_c[I][J]| over J != I.
+//   band[I][W + 1]:  o_I = sum of |J_c[I][J]| over J != I (for inspection; the LU forms each
+//                    pivot from the row's final upper entries).
 // The row sum is formed from each state's deficit 1 - sum_c p(s, c) (compensated sum), not by
 // cancelling 1 against the row's entries.  A team of PC_TEAM lanes reads one state's row (16-byte
 // loads, as the matvec does); offsets are summed 8 at a time, each lane over its entries in a
@@ -170,11 +171,11 @@ __global__ void __launch_bounds__(PC_THREADS) coarse_build_kernel(DevMDP d, cons
 
 // In-place banded LU without pivoting (unit lower L below the diagonal, U on and above) of the
 // M-matrix J_c, in the manner of Grassmann, Taksar and Heyman: every row carries its row sum s
-// and the sum o of its off-diagonal magnitudes over the Schur complement, and the pivot is
-// formed as u_kk = s_k + o_k, so every quantity is a sum of terms of one sign and FP32 keeps
-// its relative accuracy however close J_c is to singular.  Eliminating pivot k, for the rows
-// i = k+1..k+bw:  l_ik = S_ik / u_kk,  s_i += |l_ik| s_k,  o_i += -|S_ik| + |l_ik| (o_k - |u_ki|),
-// S_ij -= l_ik u_kj (i != j; diagonals are never formed until their pivot).
+// over the Schur complement, and the pivot is formed as u_kk = s_k + sum_{j>k} |u_kj| (the
+// magnitudes of the row's final upper entries), so every quantity is a sum of terms of one sign
+// and FP32 keeps its relative accuracy however close J_c is to singular.  Eliminating pivot k,
+// for the rows i = k+1..k+bw:  l_ik = S_ik / u_kk,  s_i += |l_ik| s_k,  S_ij -= l_ik u_kj
+// (i != j; diagonals are never formed by subtraction).
 // One warp: rows k..k+bw live in a shared-memory ring while pivot k is eliminated, lane r owning
 // row k+1+r, so a pivot needs one warp barrier; row k is written back when done and row
 // k+bw+1 taken from a staging buffer that cp.async fills a chunk of rows ahead.
@@ -204,18 +205,17 @@ __global__ void __launch_bounds__(32) coarse_lu_kernel(float* band, int nc, int 
   for (int k = 0; k < nc; ++k) {
     const int m = min(bw, nc - 1 - k);  // rows / columns of the trailing window
     float* rk = win + slot * Wp;
-    const float sk = rk[W], ok = rk[W + 1];
-    const float u = sk + ok;
+    const float sk = rk[W];
+    // pivot: row sum plus the magnitudes of row k's final upper entries (lanes < bw)
+    const float u = sk + warp_sum(lane < bw ? -rk[bw + 1 + lane] : 0.f);
     if (lane < m) {
       int si = slot + 1 + lane;
       if (si >= R) si -= R;
       float* ri = win + si * Wp;
       const float sik = ri[bw - 1 - lane];  // S_ik <= 0
       const float l = sik / u;              // l_ik <= 0
-      const float uki = rk[bw + 1 + lane];  // u_ki <= 0
       ri[bw - 1 - lane] = l;
       ri[W] = fmaf(-l, sk, ri[W]);
-      ri[W + 1] = fmaxf(0.f, (ri[W + 1] + sik) - l * (ok + uki));
       // row i = k+1+lane, column j = k+1+c: offset c - lane + bw in row i, c + 1 + bw in row k
       for (int c = 0; c < m; ++c)
         if (c != lane) ri[c - lane + bw] = fmaf(-l, rk[c + 1 + bw], ri[c - lane + bw]);
@@ -263,10 +263,13 @@ constexpr int LU1_AHEAD = 8;
 
 template <int BW, bool GUARD>
 __device__ __forceinline__ void lu1_pivot(float (&b)[BW + 1][2 * BW + 1], float (&sr)[BW + 1],
-                                          float (&orr)[BW + 1], float (*ring)[2 * BW + 3], int j,
-                                          int k, int nc, float* band) {
+                                          float (*ring)[2 * BW + 3], int j, int k, int nc,
+                                          float* band) {
   constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
-  const float u = sr[j] + orr[j];
+  float osum = 0.f;  // magnitudes of row k's final upper entries (all <= 0 in the band)
+#pragma unroll
+  for (int c = 1; c <= BW; ++c) osum -= b[j][BW + c];
+  const float u = sr[j] + osum;
   const float rcp = rcp_nr(u);
   b[j][BW] = u;
 #pragma unroll
@@ -277,7 +280,6 @@ __device__ __forceinline__ void lu1_pivot(float (&b)[BW + 1][2 * BW + 1], float 
       const float l = sik * rcp;
       b[q][BW - r] = l;
       sr[q] = fmaf(-l, sr[j], sr[q]);
-      orr[q] = fmaxf(0.f, (orr[q] + sik) - l * (orr[j] + b[j][BW + r]));
 #pragma unroll
       for (int c = 1; c <= BW; ++c)
         if (c != r) b[q][c - r + BW] = fmaf(-l, b[j][BW + c], b[q][c - r + BW]);
@@ -293,7 +295,6 @@ __device__ __forceinline__ void lu1_pivot(float (&b)[BW + 1][2 * BW + 1], float 
 #pragma unroll
     for (int t = 0; t < W; ++t) b[j][t] = src[t];
     sr[j] = src[W];
-    orr[j] = src[W + 1];
     const int in = i + LU1_AHEAD;  // into the slot read one pivot ago
     if (!GUARD || in < nc) {
       float* dst = ring[(in - R) % NS];
@@ -309,14 +310,13 @@ __global__ void __launch_bounds__(1) coarse_lu1_kernel(float* band, int nc) {
   constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
   __shared__ float ring[NS][Wp];
   float b[R][W];
-  float sr[R], orr[R];  // row sum and off-diagonal magnitude sum of each slot's row
+  float sr[R];  // row sum of each slot's row over its Schur complement
 #pragma unroll
   for (int r = 0; r < R; ++r) {
     const bool in = r < nc;
 #pragma unroll
     for (int t = 0; t < W; ++t) b[r][t] = in ? band[(int64_t)r * Wp + t] : 0.f;
     sr[r] = in ? band[(int64_t)r * Wp + W] : 1.f;
-    orr[r] = in ? band[(int64_t)r * Wp + W + 1] : 0.f;
   }
   for (int q = 0; q < LU1_AHEAD; ++q) {
     const int i = R + q;
@@ -330,12 +330,12 @@ __global__ void __launch_bounds__(1) coarse_lu1_kernel(float* band, int nc) {
   // every row a pivot of this round touches exists, and so does every row it prefetches
   for (; k0 + 2 * R + LU1_AHEAD + BW <= nc; k0 += R) {
 #pragma unroll
-    for (int j = 0; j < R; ++j) lu1_pivot<BW, false>(b, sr, orr, ring, j, k0 + j, nc, band);
+    for (int j = 0; j < R; ++j) lu1_pivot<BW, false>(b, sr, ring, j, k0 + j, nc, band);
   }
   for (; k0 < nc; k0 += R) {
 #pragma unroll
     for (int j = 0; j < R; ++j)
-      if (k0 + j < nc) lu1_pivot<BW, true>(b, sr, orr, ring, j, k0 + j, nc, band);
+      if (k0 + j < nc) lu1_pivot<BW, true>(b, sr, ring, j, k0 + j, nc, band);
   }
   cp_async_wait0();
 }
