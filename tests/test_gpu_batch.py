@@ -210,36 +210,6 @@ def test_batch_rejects_invalid_inputs(mg):
         assert e.value.code == -1
 
 
-def test_config4_full_size_sampled(mg):
-    """256 ELL MDPs (S log-uniform in [500, 50000], A in 2..16, k in {8, 16, 32}, gamma in
-    {0.9, 0.99, 0.999}) solved in one batch to 1e-8.  Every instance: converged, and the
-    oracle's one-state Bellman step at 16 sampled states gives |T(v)(s) - v(s)| <=
-    gamma * 1e-8 and the greedy action where the margin is clear.  The two smallest
-    instances are also solved by the oracle's PI."""
-    specs = mdp_synth.batch_specs(256, 1004)
-    syns, hs = handles_for(mg, specs)
-    b = mg.MDPBatch(hs, mg.opts(**OPTS))
-    b.tune()
-    vs, ps, sts, code = b.solve()
-    assert code == 0
-    rng = np.random.default_rng(4)
-    for syn, v, pi, st in zip(syns, vs, ps, sts):
-        assert st["status"] == 0 and st["residual_inf"] <= 1e-8, st
-        for s in rng.choice(syn.S, 16, replace=False):
-            q = np.array([syn.g[a, s] + syn.gamma * np.dot(syn.val[a, s].astype(np.float64),
-                                                           v[syn.col[a, s]])
-                          for a in range(syn.A)])
-            assert abs(q.min() - v[s]) <= syn.gamma * 1e-8 * 1.01 + 1e-12 * abs(v[s])
-            two = np.sort(q)[:2]
-            if two[1] - two[0] > 1e-6:
-                assert pi[s] == int(np.argmin(q))
-    for i in np.argsort([sp["S"] for sp in specs])[:2]:
-        m = oracle.from_synth(syns[i])
-        ref = oracle.policy_iteration(m, tol=1e-11)
-        assert rel_err(vs[i], ref.v) <= 1e-6
-        check_policy(ps[i], oracle.bellman(m, ref.v))
-
-
 def test_host_loop_equals_graph_and_batched_bellman(mg):
     """The host-driven loop runs the same kernels as the graph (results equal bit for bit);
     the batched Bellman sweep at the final V_K reproduces each instance's ||Phi_K||_inf."""

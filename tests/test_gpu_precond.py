@@ -148,27 +148,6 @@ def test_precond_rejections(mg):
     h.close()
 
 
-def test_precond_config3_full_size_sampled(mg):
-    """S=10^6, A=16, k=32 banded, FP32 values, gamma=0.999, mixed precision to 1e-8 with blocks
-    of 256 (3907 aggregates): sampled oracle Bellman steps certify the result, and the
-    preconditioned solve needs far fewer Arnoldi steps than the plain one."""
-    syn = mdp_synth.config(3)
-    h = mg.from_synth(syn)
-    v, pi, st = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed", precond_block=256))
-    assert st["status"] == 0 and st["residual_inf"] <= 1e-8, st
-    rng = np.random.default_rng(2)
-    for s in rng.choice(syn.S, 256, replace=False):
-        q = np.array([syn.g[a, s] + syn.gamma * np.dot(syn.val[a, s].astype(np.float64),
-                                                       v[syn.col[a, s]]) for a in range(syn.A)])
-        assert abs(q.min() - v[s]) <= 0.999e-8 * 1.01 + 1e-12 * abs(v[s])
-        two = np.sort(q)[:2]
-        if two[1] - two[0] > 1e-6:
-            assert pi[s] == int(np.argmin(q))
-    _, _, st0 = mg.ipi_solve(h, mg.opts(tol=1e-8, precision="mixed"))
-    assert st["inner"] * 4 <= st0["inner"], (st["inner"], st0["inner"])
-    h.close()
-
-
 @pytest.mark.parametrize("W", [2, 3])
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
 def test_precond_with_restarts_matches_oracle(mg, W, prec):
