@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fp64", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="default workload: skip the batched (config 4) and banded (config 3) "
+                         "legs reported beside the headline")
     ap.add_argument("--host-loop", action="store_true",
                     help="enqueue inner GMRES steps from the host (for profilers that cannot "
                          "follow conditional CUDA-graph nodes)")
@@ -226,36 +229,109 @@ def job_rate(units_per_rank: float, seconds_local: float, world: int, device: st
     return world * units_per_rank / max_over_ranks(seconds_local, world, device)
 
 # ---------------------------------------------------------------- CPU oracle arm
-def oracle_sample(syn_m, counts):
-    """Time a bounded sample of the oracle on the workload: one Bellman sweep and one outer
-    iteration of Alg. 2 (K=1, which ends with one more sweep); scale to a whole solve with
-    the oracle's own outer-iteration count for this workload."""
-    import oracle
-    t0 = time.perf_counter()
-    oracle.bellman(syn_m, np.zeros(syn_m.S))
-    t_sweep = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    oracle.gmres_policy_iteration(syn_m, alpha=ALPHA, W=W_, tol=TOL, K=1)
-    t_k1 = time.perf_counter() - t0
-    n_outer = int(counts["outer"]) + 1  # sweeps of a whole solve (the last one only tests)
-    t_body = max(t_k1 - 2 * t_sweep, 0.0)
-    t_solve = n_outer * t_sweep + (n_outer - 1) * t_body
-    return t_solve, t_k1 + t_sweep
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.startswith("model name") or ln.startswith("CPU part"):
+                    return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
 
 
-def oracle_counts():
-    with open(os.path.join(ROOT, "oracle", "reference_counts.json")) as f:
-        return json.load(f)["config2"]
-
-
-def cores_used():
+def cores_used() -> int:
+    """Threads the oracle's numpy/BLAS work can use in this process: the BLAS pool's size
+    when threadpoolctl can read it, else the thread-count variables, else every core."""
     try:
         import threadpoolctl
         info = threadpoolctl.threadpool_info()
-        n = max([i.get("num_threads", 1) for i in info] or [1])
-        return int(n)
+        if info:
+            return int(max(i.get("num_threads", 1) for i in info))
     except Exception:
-        return os.cpu_count() or 1
+        pass
+    for var in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS"):
+        if os.environ.get(var, "").isdigit():
+            return int(os.environ[var])
+    return os.cpu_count() or 1
+
+
+def oracle_solve_seconds(m) -> tuple[float, object]:
+    """One whole oracle iGMRES-PI solve (Alg. 2 to ||T(v)-v||_inf <= 1e-8 from V_0 = 0)."""
+    import oracle
+    t0 = time.perf_counter()
+    r = oracle.gmres_policy_iteration(m, alpha=ALPHA, W=W_, tol=TOL)
+    return time.perf_counter() - t0, r
+
+
+ONE_CORE_ENV = {"OMP_NUM_THREADS": "1", "OPENBLAS_NUM_THREADS": "1", "MKL_NUM_THREADS": "1"}
+
+
+def oracle_one_core(config: int, max_solves: int = 1) -> dict:
+    """Whole oracle solves of a workload in a child interpreter whose BLAS and OpenMP pools are
+    set to one thread before numpy loads (the paper's single-core setting, Sec. 4)."""
+    env = dict(os.environ, **ONE_CORE_ENV)
+    code = ("import sys, json; sys.path.insert(0, %r); import bench; "
+            "print(json.dumps(bench._one_core_child(%d, %d)))" % (ROOT, config, max_solves))
+    try:
+        out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True,
+                             text=True, timeout=900)
+        return json.loads(out.stdout.strip().splitlines()[-1])
+    except Exception as e:  # reported, not fatal: the all-core figure stands on its own
+        return {"error": f"one-core oracle run failed: {type(e).__name__}"}
+
+
+def _one_core_child(config: int, max_solves: int) -> dict:
+    import mdp_synth
+    import oracle
+    if config == 4:
+        specs = mdp_synth.batch_specs(256, mdp_synth.CONFIG_SEEDS[4])
+        syns = (mdp_synth.instance_from_spec(sp) for sp in specs)
+    else:
+        syns = iter([mdp_synth.config(2)])
+    secs, n = 0.0, 0
+    for syn in syns:
+        dt, _ = oracle_solve_seconds(oracle.from_synth(syn))
+        secs += dt
+        n += 1
+        if n >= max_solves:
+            break
+    return {"value": n / secs, "unit": "solves/s", "cores": cores_used(), "solves": n,
+            "seconds": secs}
+
+
+def config_fields(args, syn) -> dict:
+    """The bench line's `config` object for a single-MDP workload (both arms use it)."""
+    sb = sweep_algorithmic_bytes(syn)
+    return {"workload": workload_name(args, syn), "S": syn.S, "A": syn.A, "gamma": syn.gamma,
+            "tol": TOL, "alpha": ALPHA, "restart": W_, "forcing_c": args.forcing_c,
+            "precond_block": args.precond_block,
+            "l2": f"inputs larger than L2 (P is {sb / 1e9:.2f} GB per sweep, L2 129 MB); no flush"}
+
+
+def reference_line(args, value, total_s, config, sample, extra=None):
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000.0 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores_used(),
+                         "cpu": cpu_model(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    if extra:
+        line["cpu_baseline"].update(extra)
+    return line
 
 
 def reference_arm_batch(args):
@@ -264,37 +340,25 @@ def reference_arm_batch(args):
     import mdp_synth
     import oracle
     specs = mdp_synth.batch_specs(args.batch, mdp_synth.CONFIG_SEEDS[4])
-    total, wall = 0.0, 0.0
-    j = 0
+    total = 0.0
     for i in range(args.warmup + args.steps):
-        syn = mdp_synth.instance_from_spec(specs[j % len(specs)])
-        j += 1
-        m = oracle.from_synth(syn)
-        t0 = time.perf_counter()
-        oracle.gmres_policy_iteration(m, alpha=ALPHA, W=W_, tol=TOL)
-        dt = time.perf_counter() - t0
+        syn = mdp_synth.instance_from_spec(specs[i % len(specs)])
+        dt, _ = oracle_solve_seconds(oracle.from_synth(syn))
         if i >= args.warmup:
             total += dt
     value = args.steps / total
-    cores = cores_used()
-    sample = (f"per step: one oracle iGMRES-PI solve of the next instance of the batch "
+    sample = (f"per step: one whole oracle iGMRES-PI solve of the next instance of the batch "
               f"(instances {args.warmup}..{args.warmup + args.steps - 1} of {args.batch})")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": BATCH_WORKLOAD.format(n=args.batch)},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
-    print(json.dumps(line), flush=True)
+    cfg = {"workload": BATCH_WORKLOAD.format(n=args.batch), "instances": args.batch,
+           "tol": TOL, "alpha": ALPHA, "restart": W_}
+    print(json.dumps(reference_line(args, value, total, cfg, sample)), flush=True)
     return 0
 
 
 def reference_arm(args):
+    """The oracle on the benchmark workload: every step (warm-up and timed) is one whole
+    iGMRES-PI solve of the paper-scale dense MDP from V_0 = 0 on all host cores; afterwards one
+    more whole solve runs on one core in a child interpreter."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
@@ -302,33 +366,21 @@ def reference_arm(args):
         return reference_arm_batch(args)
     import mdp_synth
     import oracle
-    counts = oracle_counts()
-    m = oracle.from_synth(mdp_synth.config(2))
+    syn = mdp_synth.config(2)
+    m = oracle.from_synth(syn)
     for _ in range(args.warmup):
-        oracle_sample(m, counts)
+        oracle_solve_seconds(m)
     times = []
-    wall = 0.0
     for _ in range(args.steps):
-        t_solve, t_real = oracle_sample(m, counts)
-        times.append(t_solve)
-        wall += t_real
+        dt, r = oracle_solve_seconds(m)
+        times.append(dt)
     total = sum(times)
     value = args.steps / total
-    cores = cores_used()
-    sample = (f"per step: one Bellman sweep + one outer iteration of Alg. 2 (K=1) on the "
-              f"full workload, scaled to a whole solve with the oracle's own count of "
-              f"{counts['outer']} outer iterations")
-    line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
-        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": 1000.0 * total / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "l2": "inputs larger than L2"},
-        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
-        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
-                "d2h_bytes_per_step": 0},
-    }
+    sample = (f"per step: one whole oracle iGMRES-PI solve (Alg. 2, FP64 numpy) of the full "
+              f"workload from V_0 = 0 ({r.outer} outer, {r.inner} inner iterations)")
+    extra = {"p50_s": statistics.median(times), "one_core": oracle_one_core(2)}
+    line = reference_line(args, value, total, config_fields(args, syn), sample, extra)
+    line["config"]["parallelism"] = f"replicas x{args.gpus}"
     print(json.dumps(line), flush=True)
     return 0
 
@@ -356,9 +408,13 @@ def oracle_batch_sample(syns, budget_s=12.0):
     return n / t_tot, n, t_tot
 
 
-def run_batch_bench(args, mg, torch, dist, world, rank, local):
+def run_batch_bench(args, mg, torch, dist, world, rank, local, extra=False):
+    """The batched workload.  extra=True: the leg reported beside the headline line (10 timed
+    batch solves, the per-instance FP64 and mixed forms; no e2e, forcing or CPU legs); returns
+    the dict instead of printing it."""
     import mdp_synth
     n = args.batch
+    steps = 10 if extra else args.steps
     specs = mdp_synth.batch_specs(n, mdp_synth.CONFIG_SEEDS[4])
     syns = [mdp_synth.instance_from_spec(sp) for sp in specs]
     hs = [mg.from_synth(syn) for syn in syns]
@@ -386,10 +442,10 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     barrier()
     clocks = Clocks(local)
     clocks.start()
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
     stats = []
     ev[0].record(stream)
-    for i in range(args.steps):
+    for i in range(steps):
         _, _, st, code = b.solve(vd, pd)
         ev[i + 1].record(stream)
         stats.append((st, code))
@@ -397,8 +453,8 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     barrier()
     clk = clocks.stop()
     elapsed_ms = ev[0].elapsed_time(ev[-1])
-    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    value = job_rate(n * args.steps, elapsed_ms / 1000.0, world)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(steps)]
+    value = job_rate(n * steps, elapsed_ms / 1000.0, world)
     elapsed_ms = max_over_ranks(elapsed_ms, world)
     ok = all(code == 0 and all(x["status"] == 0 and x["residual_inf"] <= TOL for x in st)
              for st, code in stats)
@@ -420,7 +476,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     launches = int(sum(st[0]["launches"] for st, _ in stats))
     line = {
         "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world,
-        "steps": args.steps, "warmup": warm, "ms_per_step": elapsed_ms / args.steps,
+        "steps": steps, "warmup": warm, "ms_per_step": elapsed_ms / steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "mixed: f32 P/Krylov, double-float (2xf32) values, f64 Givens",
         "data": "synthetic",
@@ -449,7 +505,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
     }
     line["config"]["forcing_c"] = args.forcing_c
 
-    if args.forcing_c == 0.0:
+    if args.forcing_c == 0.0 and not extra:
         # the same batch with the adaptive forcing sequence (Sec. 3: alpha_k -> 0)
         ba = mg.MDPBatch(hs, mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed",
                                      forcing_c=1.0))
@@ -457,7 +513,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
         if not args.no_tune:
             ba.tune()
         ba.solve(vd, pd)
-        na = min(args.steps, 5)
+        na = min(steps, 5)
         a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a0.record(stream)
         for _ in range(na):
@@ -471,7 +527,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
                                     "inner_sum": int(sum(x["inner"] for x in sta))}
         ba.close()
 
-    if not args.no_e2e:
+    if not args.no_e2e and not extra:
         # through the host-pointer API: every step uploads every instance's P and g from pinned
         # memory (mdp_load_ell_async), solves the batch and copies every v and pi back.  Two
         # sets of handles and batches alternate, so step i+1's uploads run while step i solves.
@@ -510,7 +566,7 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
         e2e_run(2)
         torch.cuda.synchronize()
         barrier()
-        e2e_steps = min(args.steps, 4)
+        e2e_steps = min(steps, 4)
         t0 = time.perf_counter()
         e2e_run(e2e_steps)
         torch.cuda.synchronize()
@@ -558,17 +614,22 @@ def run_batch_bench(args, mg, torch, dist, world, rank, local):
         line["mixed_single"] = {"value": vmx, "unit": "solves/s", "ms_total": msmx,
                                 "form": "one ipi_solve per instance, mixed precision"}
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not extra:
         rate, m_done, secs = oracle_batch_sample(syns)
         line["cpu_baseline"] = {
-            "value": rate, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+            "value": rate, "unit": "solves/s", "cores": cores_used(), "cpu": cpu_model(),
+            "kind": "oracle",
             "sample": (f"oracle iGMRES-PI (Alg. 2) solves of the batch's first {m_done} "
                        f"instances ({secs:.1f} s of CPU); instances are i.i.d. draws")}
-    if rank == 0:
-        print(json.dumps(line), flush=True)
     b.close()
     for h in hs:
         h.close()
+    if extra:
+        for key in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data"):
+            line.pop(key, None)
+        return line
+    if rank == 0:
+        print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
     return 0
@@ -748,7 +809,8 @@ def run_serve_bench(args, mg, torch, dist, world, rank, local):
             if t_tot >= 12.0:
                 break
         line["cpu_baseline"] = {
-            "value": m_done / t_tot, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
+            "value": m_done / t_tot, "unit": "solves/s", "cores": cores_used(), "cpu": cpu_model(),
+            "kind": "oracle",
             "sample": f"oracle iGMRES-PI solves of the first {m_done} distinct request MDPs ({t_tot:.1f} s)"}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -881,10 +943,7 @@ def main():
         "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "mixed: f32 P/Krylov, double-float (2xf32) values, f64 Givens",
         "data": "synthetic",
-        "config": {"workload": workload_name(args, syn), "S": S, "A": A, "gamma": syn.gamma, "tol": TOL,
-                   "alpha": ALPHA, "restart": W_, "precision": "mixed",
-                   "parallelism": f"replicas x{world}",
-                   "l2": f"inputs larger than L2 (P is {sb / 1e9:.2f} GB per sweep, L2 129 MB); no flush"},
+        "config": dict(config_fields(args, syn), parallelism=f"replicas x{world}"),
         "converged": ok,
         "latency_ms": {"p50": float(np.percentile(step_ms, 50)), "p99": float(np.percentile(step_ms, 99))},
         "per_solve": {"outer": stats[-1]["outer"], "inner": stats[-1]["inner"],
@@ -903,8 +962,6 @@ def main():
         "gpu_launches": launches,
         "clocks": clk,
     }
-    line["config"]["forcing_c"] = args.forcing_c
-    line["config"]["precond_block"] = args.precond_block
 
     def timed_variant(ov, n):
         mg.ipi_solve(h, ov, v_out=v_out, pi_out=pi_out)
@@ -944,7 +1001,8 @@ def main():
 
     # end to end through the host-pointer API: every step uploads P and g from pinned host
     # memory (mdp_load_*_async), solves, and copies v and pi back to host arrays.  Two handles
-    # alternate, so step i+1's upload runs while step i solves.
+    # alternate, so step i+1's upload runs while step i solves.  Each step's time runs from the
+    # previous result's arrival on the host to this one's; the rate is 1 / median step.
     if not args.no_e2e:
         g_np = torch.from_numpy(np.ascontiguousarray(syn.g)).pin_memory().numpy()
         h2 = mg.from_synth(syn)
@@ -959,71 +1017,165 @@ def main():
         in_bytes = sum(int(t.numel() * t.element_size()) for t in pins) + g_np.nbytes
         v_h = np.empty(S)
         pi_h = np.empty(S, np.int32)
-        e2e_steps = min(args.steps, 8)
+        e2e_steps = max(20, args.steps)
 
         def e2e_run(k):
+            t = [time.perf_counter()]
             load(hs_e2e[0])
             for i in range(k):
                 if i + 1 < k:
                     load(hs_e2e[(i + 1) % 2])
                 mg.ipi_solve(hs_e2e[i % 2], o, v_out=v_h, pi_out=pi_h)
+                t.append(time.perf_counter())
+            return np.diff(t)
 
         e2e_run(2)
         torch.cuda.synchronize()
         barrier()
-        t0 = time.perf_counter()
-        e2e_run(e2e_steps)
+        dts = e2e_run(e2e_steps)
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
         h2.close()
-        line["e2e"] = {"value": job_rate(e2e_steps, dt, world), "unit": "solves/s",
+        med = float(np.median(dts))
+        line["e2e"] = {"value": job_rate(1, med, world), "unit": "solves/s",
                        "h2d_bytes_per_step": in_bytes,
-                       "d2h_bytes_per_step": int(v_h.nbytes + pi_h.nbytes), "steps": e2e_steps}
+                       "d2h_bytes_per_step": int(v_h.nbytes + pi_h.nbytes), "steps": e2e_steps,
+                       "median_step_ms": 1e3 * med, "mean_rate": e2e_steps / float(np.sum(dts)),
+                       "p99_step_ms": float(1e3 * np.percentile(dts, 99))}
         del pins
 
-    # the plain per-instance FP64 form on the same MDP (P widened exactly to FP64)
+    # the plain per-instance FP64 form on the same MDP (P widened exactly to FP64); its sweep
+    # does one FP64 FMA per entry, so its roofline is the GPU's measured FP64 FMA rate
     if not args.no_fp64:
-        if syn.kind == "dense":
-            syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="dense",
-                                       P=syn.P.astype(np.float64))
-        else:
-            syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="ell",
-                                       col=syn.col, val=syn.val.astype(np.float64))
-        h64 = mg.from_synth(syn64)
-        h64.set_stream(stream)
-        o64 = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="fp64")
-        mg.ipi_solve(h64, o64, v_out=v_out, pi_out=pi_out)
-        torch.cuda.synchronize()
-        n64 = 3
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(n64):
-            _, _, st64 = mg.ipi_solve(h64, o64, v_out=v_out, pi_out=pi_out)
-        e1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = e0.elapsed_time(e1) / n64
-        line["fp64_plain"] = {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_solve": ms64,
-                              "outer": st64["outer"], "inner": st64["inner"],
-                              "converged": st64["status"] == 0}
-        h64.close()
-        del syn64
+        line["fp64_plain"] = fp64_plain_leg(args, mg, torch, syn, stream, v_out, pi_out)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline and args.S == S_ and args.config == 2:
         import oracle
-        counts = oracle_counts()
         m = oracle.from_synth(syn)
-        t_solve, t_real = oracle_sample(m, counts)
+        dt, r = oracle_solve_seconds(m)
         line["cpu_baseline"] = {
-            "value": 1.0 / t_solve, "unit": "solves/s", "cores": cores_used(), "kind": "oracle",
-            "sample": (f"one Bellman sweep + one outer iteration of Alg. 2 on the full workload "
-                       f"({t_real:.1f} s of CPU), scaled to a whole solve with the oracle's own "
-                       f"{counts['outer']} outer iterations")}
+            "value": 1.0 / dt, "unit": "solves/s", "cores": cores_used(), "cpu": cpu_model(),
+            "kind": "oracle",
+            "sample": (f"one whole oracle iGMRES-PI solve (Alg. 2, FP64 numpy) of the full "
+                       f"workload from V_0 = 0 ({r.outer} outer, {r.inner} inner iterations, "
+                       f"{dt:.1f} s)"),
+            "one_core": oracle_one_core(2)}
+        del m
+
+    # the other benchmark workloads beside the headline: the batch of 256 uneven MDPs (with the
+    # plain per-instance FP64 form on the same MDPs) and the banded S = 10^6 MDP
+    if args.config == 2 and args.S == S_ and not args.no_extras:
+        h.close()
+        h = None
+        del syn
+        line["config4_batched"] = run_batch_bench(args, mg, torch, dist, world, rank, local,
+                                                  extra=True)
+        line["config3_banded"] = banded_leg(args, mg, torch, stream)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    h.close()
+    if h is not None:
+        h.close()
     if world > 1:
         dist.destroy_process_group()
     return 0
+
+
+def fp64_plain_leg(args, mg, torch, syn, stream, v_out, pi_out, n64=10):
+    import mdp_synth
+    S, A = syn.S, syn.A
+    if syn.kind == "dense":
+        syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="dense",
+                                   P=syn.P.astype(np.float64))
+    else:
+        syn64 = mdp_synth.SynthMDP(S=S, A=A, gamma=syn.gamma, g=syn.g, kind="ell",
+                                   col=syn.col, val=syn.val.astype(np.float64))
+    h64 = mg.from_synth(syn64)
+    del syn64
+    h64.set_stream(stream)
+    o64 = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="fp64",
+                  precond_block=args.precond_block)
+    mg.ipi_solve(h64, o64, v_out=v_out, pi_out=pi_out)
+    torch.cuda.synchronize()
+    h64.set_timing(True)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(n64 + 1)]
+    ev[0].record(stream)
+    sts = []
+    for i in range(n64):
+        _, _, st64 = mg.ipi_solve(h64, o64, v_out=v_out, pi_out=pi_out)
+        ev[i + 1].record(stream)
+        sts.append(st64)
+    torch.cuda.synchronize()
+    h64.set_timing(False)
+    h64.close()
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(n64)]
+    ms64 = ev[0].elapsed_time(ev[-1]) / n64
+    sweeps = sum(s["timed_sweeps"] for s in sts)
+    sweep_ms = sum(s["sweep_ms"] for s in sts) / max(1, sweeps)
+    nnz = S * A * (S if syn.kind == "dense" else syn.k)
+    flops = 2.0 * nnz                         # one FMA per transition entry
+    bytes64 = nnz * (8 if syn.kind == "dense" else 12) + A * S * 8 + S * 24
+    tf = flops / (sweep_ms * 1e-3) / 1e12 if sweep_ms > 0 else 0.0
+    fp64_peak = mg.probe_alu("f64")
+    hbm_peak, kind = peaks()
+    return {"value": 1000.0 / ms64, "unit": "solves/s", "ms_per_solve": ms64, "solves": n64,
+            "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                           "p99": float(np.percentile(step_ms, 99))},
+            "outer": sts[-1]["outer"], "inner": sts[-1]["inner"],
+            "converged": all(s["status"] == 0 and s["residual_inf"] <= TOL for s in sts),
+            "form": "ipi_solve with P widened exactly to FP64, FP64 Krylov vectors and sums",
+            "sweep": {"ms": sweep_ms, "algorithmic_flops": flops, "algorithmic_bytes": bytes64,
+                      "gbs": bytes64 / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0},
+            "roofline": {"bound": "alu", "kernel": ("sweep_dense_kernel (FP64)" if syn.kind == "dense"
+                                                    else "sweep_ell (FP64)"),
+                         "achieved": tf, "peak": fp64_peak, "unit": "TFLOP/s",
+                         "frac": tf / fp64_peak if fp64_peak else None,
+                         "peak_source": "measured FP64 FMA rate (mdp_probe_alu, this run)",
+                         "hbm_frac": (bytes64 / (sweep_ms * 1e-3) / 1e9) / hbm_peak
+                         if sweep_ms > 0 else None}}
+
+
+def banded_leg(args, mg, torch, stream):
+    """Config 3 (S = 10^6 banded ELL, gamma = 0.999) beside the headline: the two-level
+    preconditioned solve (blocks of 512) and plain Alg. 2, with the windowed sweep's HBM
+    rate from CUDA events on the handle's stream."""
+    import mdp_synth
+    syn = mdp_synth.config(3)
+    h = mg.from_synth(syn)
+    h.set_stream(stream)
+    vo = torch.empty(syn.S, dtype=torch.float64, device="cuda")
+    po = torch.empty(syn.S, dtype=torch.int32, device="cuda")
+    out = {"workload": workload_name(argparse.Namespace(config=3), syn), "S": syn.S, "A": syn.A,
+           "k": syn.k, "gamma": syn.gamma}
+    peak, kind = peaks()
+    for name, pb, n in (("two_level_precond", 512, 10), ("plain", 0, 2)):
+        o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", precond_block=pb)
+        mg.ipi_solve(h, o, v_out=vo, pi_out=po)
+        torch.cuda.synchronize()
+        h.set_timing(True)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        ev[0].record(stream)
+        sts = []
+        for i in range(n):
+            _, _, st = mg.ipi_solve(h, o, v_out=vo, pi_out=po)
+            ev[i + 1].record(stream)
+            sts.append(st)
+        torch.cuda.synchronize()
+        h.set_timing(False)
+        step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+        sweeps = sum(s["timed_sweeps"] for s in sts)
+        sweep_ms = sum(s["sweep_ms"] for s in sts) / max(1, sweeps)
+        gbs = sweep_algorithmic_bytes(syn) / (sweep_ms * 1e-3) / 1e9 if sweep_ms > 0 else 0.0
+        out[name] = {"precond_block": pb, "value": n / (ev[0].elapsed_time(ev[-1]) / 1000.0),
+                     "unit": "solves/s", "solves": n,
+                     "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                                    "p99": float(np.percentile(step_ms, 99))},
+                     "outer": sts[-1]["outer"], "inner": sts[-1]["inner"],
+                     "converged": all(s["status"] == 0 and s["residual_inf"] <= TOL for s in sts)}
+        if name == "plain":
+            out["bellman_sweep"] = {"kernel": sweep_kernel_name(syn), "ms": sweep_ms, "gbs": gbs,
+                                    "algorithmic_bytes": sweep_algorithmic_bytes(syn),
+                                    "frac": gbs / peak, "peak": peak, "peak_source": kind}
+    h.close()
+    return out
 
 
 if __name__ == "__main__":

@@ -39,7 +39,10 @@ enum mdp_status {
   MDP_ENOCONV = -3,   /* iteration cap reached before the stopping rule held */
   MDP_EDEVICE = -4,   /* CUDA runtime error */
   MDP_ETIMEOUT = -5,  /* a bounded device wait ran out */
-  MDP_EBREAKDOWN_INFO = 1 /* informational: GMRES met a (lucky) breakdown; result valid */
+  MDP_EBREAKDOWN_INFO = 1 /* informational success, returned by policy_eval_gmres when the
+                           * target was met and its last inner GMRES solve ended by a lucky
+                           * breakdown (the result is exact in the Krylov space); the solvers
+                           * count breakdowns in mdp_stats.breakdowns and return MDP_OK */
 };
 
 enum mdp_dtype { MDP_F32 = 0, MDP_F64 = 1 };
@@ -163,7 +166,9 @@ typedef struct {
   int32_t timed_sweeps; /* sweep launches covered by sweep_ms */
   int32_t timed_matvecs;/* matvec launches covered by matvec_ms */
   int32_t launches;     /* kernels launched by the call */
-  int32_t reserved;
+  int32_t breakdowns;   /* inner GMRES solves that ended by a lucky breakdown (Alg. 2's
+                         * "||q||_2 = 0" branch: the Krylov space is invariant, so the least-
+                         * squares iterate solves the inner system exactly) */
 } mdp_stats;
 
 /* Kernel shape for ELL data: lanes that share one row in the Bellman sweep and in the P^pi
@@ -217,7 +222,10 @@ int bellman_apply_dev(mdp_t h, const double* v, double* Tv, int32_t* pi, double*
  * work.  Errors are reported by the return code only (MDP_EINVAL for bad sizes or null
  * pointers, MDP_EDEVICE for CUDA errors); mdp_last_error is not updated, since storing a
  * message could allocate host memory.  The first call on a device looks the scratch address
- * up (cudaGetSymbolAddress), so make that first call before any stream capture.  All calls
+ * up (cudaGetSymbolAddress), so make that first call before any stream capture.  The address
+ * is cached per device for the life of the process: cudaDeviceReset (or anything else that
+ * destroys the primary context) unloads the device image it points into, so after such a reset
+ * this entry point must not be called again in that process.  All calls
  * share the scratch, which keeps the last call's contents; each call clears the counters it
  * needs on its own stream first, and calls whose work overlaps on the GPU (unordered streams)
  * race on it.  Work is enqueued on `stream` (a cudaStream_t; NULL = legacy default stream)
@@ -362,6 +370,29 @@ int mdp_server_drain(mdp_server_t s);
 /* Requests holding a slot, requests waiting, device bytes admitted, loop launches so far. */
 int mdp_server_info(mdp_server_t s, int32_t* active, int32_t* pending, int64_t* bytes_in_use,
                     int64_t* launches);
+
+/* Inspection of the two-level preconditioner (the preconditioned policy evaluation that
+ * ipi_solve runs with mdp_opts.precond_block; preconditioning is named as future work in
+ * Sec. 5).  For the policy pi[S] (host or device pointer, every entry an allowed action) and
+ * aggregation blocks of `block` states (a power of two in [2, S]), builds the Galerkin coarse
+ * operator J_c = R (I - gamma P^pi) Pr, factors it and forms J_c^{-1} in FP32 exactly as the
+ * solver does once per policy, and copies J_c^{-1} row-major into inv_out[nc * nc] (host;
+ * NULL = size query only).  *nc_out = number of coarse blocks ceil(S / block), *bw_out = the
+ * band half-width of J_c in blocks (either may be NULL).  ELL handles only.  Returns MDP_EINVAL
+ * for dense data, a bad block, a policy entry out of range, more than 8192 blocks or a band
+ * wider than 31 blocks; the handle's solver workspace is reused. */
+int mdp_precond_coarse_inverse(mdp_t h, const int32_t* pi, int32_t block, float* inv_out,
+                               int64_t* nc_out, int32_t* bw_out);
+
+/* Arithmetic-rate probe (no counterpart in the paper; it states the peak against which the
+ * plain FP64 form's sweep is measured, since on this GPU that form can be bound by FP64
+ * arithmetic rather than by HBM).  Runs eight independent FMA chains per thread over a grid of
+ * 8 blocks per SM on the current device, in the given dtype (MDP_F64 or MDP_F32), and writes
+ * the best of three timed launches to *tflops (2 flops per FMA).  Allocates a small scratch
+ * buffer and a private stream for the duration of the call and synchronises on it; about 0.1 s
+ * for FP64.  Returns MDP_EINVAL for another dtype or a NULL output, MDP_EDEVICE/ENOMEM on CUDA
+ * failures. */
+int mdp_probe_alu(int32_t dtype, double* tflops);
 
 /* Message for the last nonzero return on this thread ("" if none). */
 const char* mdp_last_error(void);

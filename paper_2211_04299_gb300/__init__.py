@@ -423,3 +423,24 @@ class MDPServer:
         _check(lib().mdp_server_info(self.ptr, C.byref(a), C.byref(p), C.byref(b), C.byref(l)),
                "mdp_server_info")
         return {"active": a.value, "pending": p.value, "bytes_in_use": b.value, "launches": l.value}
+
+
+def probe_alu(dtype: str = "f64") -> float:
+    """Measured FMA rate of the current GPU in TFLOP/s (mdp_probe_alu), "f64" or "f32"."""
+    out = C.c_double(0.0)
+    _check(lib().mdp_probe_alu(MDP_F64 if dtype == "f64" else MDP_F32, C.byref(out)),
+           "mdp_probe_alu")
+    return out.value
+
+
+def precond_coarse_inverse(h: MDPHandle, pi, block: int):
+    """J_c^{-1} of the two-level preconditioner for policy pi (mdp_precond_coarse_inverse)
+    -> (inverse as an (nc, nc) float32 array, band half-width in blocks)."""
+    pi = np.ascontiguousarray(pi, dtype=np.int32)
+    nc, bw = C.c_int64(), C.c_int32()
+    _check(lib().mdp_precond_coarse_inverse(h.ptr, _ptr(pi), int(block), None, C.byref(nc),
+                                            C.byref(bw)), "mdp_precond_coarse_inverse")
+    inv = np.empty((nc.value, nc.value), dtype=np.float32)
+    _check(lib().mdp_precond_coarse_inverse(h.ptr, _ptr(pi), int(block), _ptr(inv), C.byref(nc),
+                                            C.byref(bw)), "mdp_precond_coarse_inverse")
+    return inv, bw.value

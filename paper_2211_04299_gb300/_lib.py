@@ -39,10 +39,10 @@ class mdp_stats(C.Structure):
                 ("residual_inf", C.c_double), ("seconds", C.c_double), ("bytes", C.c_double),
                 ("sweep_ms", C.c_double), ("matvec_ms", C.c_double),
                 ("timed_sweeps", C.c_int32), ("timed_matvecs", C.c_int32),
-                ("launches", C.c_int32), ("reserved", C.c_int32)]
+                ("launches", C.c_int32), ("breakdowns", C.c_int32)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 _vp = C.c_void_p
@@ -52,6 +52,8 @@ _h = C.c_void_p
 
 # name -> (restype, argtypes); every symbol include/mdpgpu.h declares
 SIGNATURES = {
+    "mdp_precond_coarse_inverse": (C.c_int, [_h, _vp, C.c_int32, _vp, C.POINTER(C.c_int64), _ip]),
+    "mdp_probe_alu": (C.c_int, [C.c_int32, _dp]),
     "mdp_create_dense": (C.c_int, [C.c_int64, C.c_int32, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),
     "mdp_create_ell": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),
     "mdp_create_dense_dev": (C.c_int, [C.c_int64, C.c_int32, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),

@@ -1,0 +1,81 @@
+// Arithmetic-rate probe: mdp_probe_alu.
+//
+// The plain FP64 form of the solver accumulates every transition entry with an FP64 FMA, and
+// GB300's FP64 pipe is a small fraction of its FP32 pipe, so that form's Bellman sweep can be
+// bound by FP64 arithmetic rather than by HBM.  This probe measures the FMA rate of the GPU it
+// runs on, so that such a kernel's roofline is stated against a measured peak: every thread
+// keeps eight independent FMA chains (no dependency stalls between them), the grid covers
+// every SM several times over, and the rate is 2 flops per FMA over the best of three timed
+// launches (CUDA events on a private stream, after one warm-up launch).
+#include "mdp_internal.cuh"
+
+namespace {
+
+constexpr int PR_THREADS = 256;
+constexpr int PR_CHAINS = 8;
+
+template <typename T>
+__global__ void __launch_bounds__(PR_THREADS)
+fma_chains_kernel(int iters, T m, T a, T* out) {
+  T x[PR_CHAINS];
+#pragma unroll
+  for (int c = 0; c < PR_CHAINS; ++c) x[c] = (T)(threadIdx.x + c) * (T)1e-3;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int c = 0; c < PR_CHAINS; ++c) x[c] = fma(x[c], m, a);
+  }
+  T s = 0;
+#pragma unroll
+  for (int c = 0; c < PR_CHAINS; ++c) s += x[c];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;  // keeps the chains live
+}
+
+template <typename T>
+int probe(int iters, double* tflops) {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return mdp::set_error(MDP_EDEVICE, "mdp_probe_alu: no device");
+  const int blocks = sms * 8;
+  T* out = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  int r = MDP_OK;
+  if (cudaMalloc(&out, (size_t)blocks * PR_THREADS * sizeof(T)) != cudaSuccess)
+    return mdp::set_error(MDP_ENOMEM, "mdp_probe_alu: cudaMalloc failed");
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    r = mdp::set_error(MDP_EDEVICE, "mdp_probe_alu: stream or event creation failed");
+  }
+  float best = 0.f;
+  for (int rep = 0; rep < 4 && r == MDP_OK; ++rep) {
+    cudaEventRecord(e0, st);
+    fma_chains_kernel<T><<<blocks, PR_THREADS, 0, st>>>(iters, (T)0.999999, (T)1e-7, out);
+    cudaEventRecord(e1, st);
+    if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+      r = mdp::set_error(MDP_EDEVICE, "mdp_probe_alu: launch failed");
+      break;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && (best == 0.f || ms < best)) best = ms;  // rep 0 is the warm-up
+  }
+  if (r == MDP_OK) {
+    const double flops = 2.0 * PR_CHAINS * (double)iters * blocks * PR_THREADS;
+    *tflops = flops / (best * 1e-3) / 1e12;
+  }
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (st) cudaStreamDestroy(st);
+  cudaFree(out);
+  return r;
+}
+
+}  // namespace
+
+extern "C" int mdp_probe_alu(int32_t dtype, double* tflops) {
+  if (!tflops) return mdp::set_error(MDP_EINVAL, "mdp_probe_alu: null output");
+  if (dtype == MDP_F64) return probe<double>(20000, tflops);
+  if (dtype == MDP_F32) return probe<float>(400000, tflops);
+  return mdp::set_error(MDP_EINVAL, "mdp_probe_alu: dtype must be MDP_F32 or MDP_F64");
+}

@@ -53,3 +53,19 @@ def test_traffic_lookup_needs_the_current_source_hash(tmp_path, monkeypatch):
 
 def test_job_rate_single_rank():
     assert abs(bench.job_rate(20, 2.0, 1) - 10.0) < 1e-12
+
+
+def test_both_arms_share_the_config_object():
+    """The oracle arm's line carries the same config keys and values as the GPU arm's (the
+    GPU arm adds nothing else to config), with the CPU model and core count beside it."""
+    import argparse
+    args = argparse.Namespace(config=2, S=bench.S_, forcing_c=0.0, precond_block=0, gpus=1,
+                              steps=2, warmup=0)
+    syn = mdp_synth.dense_dirichlet(64, 8, 0.1, bench.GAMMA, seed=1)
+    cfg = dict(bench.config_fields(args, syn), parallelism="replicas x1")
+    line = bench.reference_line(args, 0.5, 4.0, cfg, "sample")
+    assert line["config"] == cfg
+    for key in ("S", "A", "gamma", "tol", "alpha", "restart", "workload"):
+        assert key in cfg
+    assert line["cpu_baseline"]["cpu"] and line["cpu_baseline"]["cores"] >= 1
+    assert line["ms_per_step"] == 2000.0

@@ -4,7 +4,8 @@ Every state of every result is checked, in the launch configurations bench.py ti
   * config 2 (dense S=10^4, A=8, gamma=0.99): the whole v of the mixed solve (1e-6 relative)
     and of the plain FP64 solve at the tightened tolerance of reading A13 (1e-10 relative)
     against the oracle's Alg. 2 run to 1e-13; policies against the oracle's;
-  * config 3 (banded S=10^6, A=16, k=32, gamma=0.999), plain and two-level preconditioned;
+  * config 3 (banded S=10^6, A=16, k=32, gamma=0.999), plain and two-level preconditioned,
+    whole v against the oracle's preconditioned Alg. 2 run to 1e-9;
   * config 4 (256 uneven ELL MDPs in one batch) in the mixed form and in the plain per-instance
     FP64 form;
   * config 5 (requests of the serving distribution at full size) through the serving loop.
@@ -103,20 +104,28 @@ def test_config2_fp64_plain_whole_vector(mg, cfg2):
 # ------------------------------------------------------------------ config 3
 @pytest.fixture(scope="module")
 def cfg3(mg):
+    """The oracle's own solve of config 3: Alg. 2 with the two-level preconditioned inner
+    GMRES (blocks of 512; plain Alg. 2 needs thousands of MGS steps at gamma = 0.999), to
+    ||T v - v|| <= 1e-9, so that its values are within 1e-6 absolute of V*."""
     syn = mdp_synth.config(3)
-    return syn, oracle.from_synth(syn), mg.from_synth(syn)
+    m = oracle.from_synth(syn)
+    ref = oracle.gmres_policy_iteration(m, alpha=ALPHA, W=W, tol=1e-9, precond_block=512)
+    assert ref.status == "ok"
+    return syn, m, mg.from_synth(syn), ref
 
 
 def test_config3_every_state(mg, cfg3):
     """S=10^6 banded, gamma=0.999, mixed: plain Alg. 2 and the two-level preconditioned inner
     solve with blocks of 512 states (the bench's two forms); the preconditioned solve also
     needs at least 4x fewer Arnoldi steps."""
-    syn, m, h = cfg3
+    syn, m, h, ref = cfg3
     inner = {}
     for pb in (0, 512):
         v, pi, st = mg.ipi_solve(h, mg.opts(tol=TOL, alpha=ALPHA, restart=W, precision="mixed",
                                             precond_block=pb))
         assert st["status"] == 0 and st["residual_inf"] <= TOL, (pb, st)
+        assert rel_err(v, ref.v) <= 1e-6
+        policy_against_reference(pi, ref, st["residual_inf"], syn.gamma)
         sw, _ = certify_solution(m, v, pi, st["residual_inf"], 1e-6)
         Tv, pis, res = mg.bellman_apply(h, v, precision="mixed")
         check_sweep(sw, Tv, pis, res, 1e-12)
