@@ -286,7 +286,7 @@ int ensure_pc(mdp_t h, int kt, int W, int lb) {
   p.ldc = round_up(nc, 4);
   const size_t ek = kt ? 4 : 8;
   size_t& acc = p.bytes;
-  RK(alloc0((void**)&p.band, (size_t)nc * (2 * bw + 3) * 4, acc));
+  RK(alloc0((void**)&p.band, (size_t)nc * (2 * bw + 2) * 4, acc));
   RK(alloc0((void**)&p.cl, (size_t)nc * 32 * 4, acc));
   RK(alloc0((void**)&p.cu, (size_t)nc * 32 * 4, acc));
   RK(alloc0((void**)&p.dinv, (size_t)nc * 4, acc));
@@ -502,6 +502,7 @@ int inner_gmres(mdp_t h, const int32_t* pi_dev, int slot, double alpha, double t
     // CGS2: three passes over Q_0..Q_i plus w traffic, per step (i averaged over the cycle)
     const double avg_m = std::min<double>(W, hc.steps) * 0.5 + 1.0;
     st->bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * ek2;
+    if (hc.status == GS_BREAKDOWN) st->breakdowns += 1;
   }
   if (status_out) *status_out = hc.status;
   return MDP_OK;
@@ -712,7 +713,7 @@ enum Method { METH_IPI = 0, METH_VI = 1, METH_PI = 2, METH_OPI = 3, METH_IPI_VI 
 // (one solve in FP64; in FP32 Krylov each solve cuts the residual by up to 1e-5 and the
 // next residual is recomputed in double-float).
 int eval_policy(mdp_t h, const int32_t* pi_dev, int arith, double target, const mdp_opts& o,
-                mdp_stats* st, double* final_res) {
+                mdp_stats* st, double* final_res, int* last_status = nullptr) {
   Workspace& w = h->ws;
   const double floor_rel = arith ? 1e-5 : 0.0;
   double res = INFINITY, prev = INFINITY;
@@ -728,6 +729,7 @@ int eval_policy(mdp_t h, const int32_t* pi_dev, int arith, double target, const 
     const double thr = std::max(target, floor_rel * res);
     int status = 0;
     RK(inner_gmres(h, pi_dev, 1, 0.0, thr, o.restart, o.max_inner, st, &status));
+    if (last_status) *last_status = status;
     if (status == GS_CAP && !arith) break;
   }
   if (final_res) *final_res = res;
@@ -788,6 +790,7 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
       st.inner += hc.steps;
       st.restarts += hc.restarts;
       st.matvecs += hc.steps + hc.checks;
+      if (hc.status == GS_BREAKDOWN) st.breakdowns += 1;
       st.bytes += (double)(hc.steps + hc.checks) * matvec_bytes(h, w.kt);
       const double avg_m = std::min<double>(o.restart, hc.steps) * 0.5 + 1.0;
       st.bytes += hc.steps * (3.0 * avg_m + 6.0) * (double)S * (w.kt ? 4.0 : 8.0);
@@ -1247,17 +1250,19 @@ int policy_eval_gmres_dev(mdp_t h, const int32_t* pi, const double* v0, double t
   }
   RK(load_v(h, v0, arith));
   double res = 0;
-  RK(eval_policy(h, w.pi2, arith, target_inf, o, &st, &res));
+  int last = GS_RUNNING;
+  RK(eval_policy(h, w.pi2, arith, target_inf, o, &st, &res, &last));
   RK(store_v(h, w.v, v_out, arith));
   CK(cudaStreamSynchronize(h->stream));
   RK(check_device_error(h));
   collect_times(h, &st);
   st.residual_inf = res;
-  st.status = res <= target_inf ? MDP_OK : MDP_ENOCONV;
+  st.status = res <= target_inf ? (last == GS_BREAKDOWN ? MDP_EBREAKDOWN_INFO : MDP_OK)
+                                 : MDP_ENOCONV;
   st.launches = h->launches;
   st.seconds = now_s() - t0;
   if (stats) *stats = st;
-  if (st.status != MDP_OK) g_err = "policy evaluation did not reach the target";
+  if (st.status == MDP_ENOCONV) g_err = "policy evaluation did not reach the target";
   return st.status;
 }
 
@@ -1265,6 +1270,40 @@ int policy_eval_gmres(mdp_t h, const int32_t* pi, const double* v0, double targe
                       const mdp_opts* opts, double* v_out, mdp_stats* stats) {
   // host pointers: cudaMemcpyDefault handles them through the same path
   return policy_eval_gmres_dev(h, pi, v0, target_inf, opts, v_out, stats);
+}
+
+// Coarse inverse of the two-level preconditioner for a given policy, copied to the host: the
+// same band build, GTH-form LU and explicit FP32 inverse that ipi_solve runs once per policy.
+int mdp_precond_coarse_inverse(mdp_t h, const int32_t* pi, int32_t block, float* inv_out,
+                               int64_t* nc_out, int32_t* bw_out) {
+  if (h && h->vpending) RK(finish_upload(h));
+  g_err.clear();
+  if (!h || !pi) return fail(MDP_EINVAL, "null handle or policy");
+  if (h->d.kind != KIND_ELL) return fail(MDP_EINVAL, "the two-level preconditioner needs ELL data");
+  if (block < 2 || (block & (block - 1)) != 0 || (int64_t)block > h->d.S)
+    return fail(MDP_EINVAL, "block must be a power of two in [2, S]");
+  const int kt = h->d.pdt == MDP_F32 ? 1 : 0;
+  RK(ensure_ws(h, kt, 1));
+  RK(ensure_pc(h, kt, 1, log2_exact(block)));
+  Workspace& w = h->ws;
+  auto& p = h->pc;
+  CK(cudaMemcpyAsync(w.pi2, pi, (size_t)h->d.S * 4, cudaMemcpyDefault, h->stream));
+  CK(cudaMemsetAsync(w.flags, 0, 64, h->stream));
+  RK(launch_check_policy(w.pi2, h->d.S, h->d.A, h->d.mask, w.flags, h->stream));
+  int hf[16] = {0};
+  CK(cudaMemcpyAsync(hf, w.flags, 64, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (hf[5]) return fail(MDP_EINVAL, "policy entry out of range or not an allowed action");
+  RK(launch_coarse_setup(h->d, w.pi2, pck(h), p.bw,
+                         PrecondScratch{p.band, p.cl, p.cu, p.dinv}, h->stream));
+  if (inv_out)
+    CK(cudaMemcpy2DAsync(inv_out, (size_t)p.nc * 4, p.inv, (size_t)p.ldc * 4, (size_t)p.nc * 4,
+                         (size_t)p.nc, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  RK(check_device_error(h));
+  if (nc_out) *nc_out = p.nc;
+  if (bw_out) *bw_out = p.bw;
+  return MDP_OK;
 }
 
 #define SOLVER(name, method)                                                            \

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_init_kernel(BatchDev B) {
     I.status = MDP_ENOCONV;
     I.starting = 0;
     I.rhs_sel = 0;
-    I.inner = I.restarts = I.checks = I.sweeps = I.loops = 0;
+    I.inner = I.restarts = I.checks = I.sweeps = I.loops = I.breakdowns = 0;
     I.thr = 0.0;
     I.res = 0.0;
     I.ctl->mode = GM_IDLE;
@@ -153,6 +153,7 @@ __global__ void __launch_bounds__(CTRL_THREADS) batch_ctrl_kernel(BatchDev B) {
       I.restarts += c->restarts;
       I.checks += c->checks;
       I.loops += 1;
+      if (c->status == GS_BREAKDOWN) I.breakdowns += 1;
       if (c->mode != GM_DONE) {  // cannot happen: SWEEPV follows a finished solve
         I.status = MDP_ETIMEOUT;
         I.phase = BP_DONE;
@@ -648,6 +649,7 @@ int run_batch(mdp_batch_s* b, double* const* v_out, int32_t* const* pi_out, mdp_
     s.restarts = I.restarts;
     s.sweeps = I.sweeps;
     s.matvecs = I.inner + I.checks;
+    s.breakdowns = I.breakdowns;
     s.status = I.phase == BP_DONE ? I.status : MDP_ETIMEOUT;
     s.residual_inf = I.res;
     s.launches = 3 + iters * b->launches_per_iter;
@@ -916,7 +918,7 @@ void batch_reset_state(BatchInst& I) {
   I.status = MDP_ENOCONV;
   I.starting = 0;
   I.rhs_sel = 0;
-  I.inner = I.restarts = I.checks = I.sweeps = I.loops = 0;
+  I.inner = I.restarts = I.checks = I.sweeps = I.loops = I.breakdowns = 0;
   I.thr = 0.0;
   I.res = 0.0;
 }

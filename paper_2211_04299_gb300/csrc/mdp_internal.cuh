@@ -577,7 +577,7 @@ struct BatchInst {
   int cls_sw, cls_mv;              // ELL lane class of the sweep / matvec
   // state
   int phase, cur, k, reps, status, starting, rhs_sel;
-  int inner, restarts, checks, sweeps, loops;
+  int inner, restarts, checks, sweeps, loops, breakdowns;
   double thr, res;
 };
 

@@ -56,11 +56,10 @@ __global__ void coarse_bandwidth_kernel(DevMDP d, int lb, int* bw) {
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(bw, m);
 }
 
-// Row I of the coarse operator (one block per coarse row), stored as Wp = 2 bw + 3 floats:
+// Row I of the coarse operator (one block per coarse row), stored as Wp = 2 bw + 2 floats:
 //   band[I][t], t = J - I + bw < W:  J_c[I][J] = delta_{IJ} - gamma / |I| * sum_{s in I} sum_{c in J} p(s, c)
 //   band[I][W]:      s_I = row sum of J_c = (1 - gamma) + gamma * mean_{s in I} (1 - sum_c p(s, c))
-//   band[I][W + 1]:  o_I = sum of |J_c[I][J]| over J != I (for inspection; the LU forms each
-//                    pivot from the row's final upper entries).
+// (the LU forms each pivot from s_I and the row's final upper entries, never from the diagonal).
 // The row sum is formed from each state's deficit 1 - sum_c p(s, c) (compensated sum), not by
 // cancelling 1 against the row's entries.  A team of PC_TEAM lanes reads one state's row (16-byte
 // loads, as the matvec does); offsets are summed 8 at a time, each lane over its entries in a
@@ -71,7 +70,7 @@ template <class PT>
 __global__ void __launch_bounds__(PC_THREADS) coarse_build_kernel(DevMDP d, const int32_t* pi, int lb,
                                                                   int bw, float* band) {
   __shared__ float red[PC_THREADS / 32][9];
-  const int W = 2 * bw + 1, Wp = W + 2;
+  const int W = 2 * bw + 1, Wp = W + 1;
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const int team = threadIdx.x / PC_TEAM, tl = threadIdx.x % PC_TEAM;
   const int nteams = PC_THREADS / PC_TEAM;
@@ -161,12 +160,6 @@ __global__ void __launch_bounds__(PC_THREADS) coarse_build_kernel(DevMDP d, cons
     }
     __syncthreads();
   }
-  if (threadIdx.x == 0) {  // o_I from the stored (FP32) off-diagonals the LU will use
-    double o = 0.0;
-    for (int t = 0; t < W; ++t)
-      if (t != bw) o -= (double)band[I * Wp + t];
-    band[I * Wp + W + 1] = (float)o;
-  }
 }
 
 // In-place banded LU without pivoting (unit lower L below the diagonal, U on and above) of the
@@ -181,7 +174,7 @@ __global__ void __launch_bounds__(PC_THREADS) coarse_build_kernel(DevMDP d, cons
 // k+bw+1 taken from a staging buffer that cp.async fills a chunk of rows ahead.
 __global__ void __launch_bounds__(32) coarse_lu_kernel(float* band, int nc, int bw) {
   extern __shared__ float sm[];
-  const int W = 2 * bw + 1, Wp = W + 2, R = bw + 1;
+  const int W = 2 * bw + 1, Wp = W + 1, R = bw + 1;
   const int lane = threadIdx.x;
   float* win = sm;             // [R][Wp] ring, row r in slot r % R
   float* stg = sm + R * Wp;    // [2][LU_CHUNK][Wp]; chunk c holds rows R + c*LU_CHUNK ...
@@ -263,9 +256,9 @@ constexpr int LU1_AHEAD = 8;
 
 template <int BW, bool GUARD>
 __device__ __forceinline__ void lu1_pivot(float (&b)[BW + 1][2 * BW + 1], float (&sr)[BW + 1],
-                                          float (*ring)[2 * BW + 3], int j, int k, int nc,
+                                          float (*ring)[2 * BW + 2], int j, int k, int nc,
                                           float* band) {
-  constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
+  constexpr int W = 2 * BW + 1, Wp = W + 1, R = BW + 1, NS = LU1_AHEAD + 1;
   float osum = 0.f;  // magnitudes of row k's final upper entries (all <= 0 in the band)
 #pragma unroll
   for (int c = 1; c <= BW; ++c) osum -= b[j][BW + c];
@@ -307,7 +300,7 @@ __device__ __forceinline__ void lu1_pivot(float (&b)[BW + 1][2 * BW + 1], float 
 
 template <int BW>
 __global__ void __launch_bounds__(1) coarse_lu1_kernel(float* band, int nc) {
-  constexpr int W = 2 * BW + 1, Wp = W + 2, R = BW + 1, NS = LU1_AHEAD + 1;
+  constexpr int W = 2 * BW + 1, Wp = W + 1, R = BW + 1, NS = LU1_AHEAD + 1;
   __shared__ float ring[NS][Wp];
   float b[R][W];
   float sr[R];  // row sum of each slot's row over its Schur complement
@@ -345,7 +338,7 @@ __global__ void __launch_bounds__(1) coarse_lu1_kernel(float* band, int nc) {
 //   forward  L y = e_j:  y[k] = delta_{kj} + sum_q cl[k][q] y[k-1-q],   cl[k][q] = -L[k][k-1-q]
 //   backward U x = y:    x[k] = dinv[k] y[k] + sum_q cu[k][q] x[k+1+q], cu[k][q] = -U[k][k+1+q] dinv[k]
 __global__ void coarse_prep_kernel(const float* band, int nc, int bw, float* cl, float* cu, float* dinv) {
-  const int W = 2 * bw + 1, Wp = W + 2;
+  const int W = 2 * bw + 1, Wp = W + 1;
   for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < (int64_t)nc * 32;
        e += (int64_t)gridDim.x * blockDim.x) {
     const int k = (int)(e >> 5), q = (int)(e & 31);
@@ -580,7 +573,7 @@ int launch_coarse_bandwidth(const DevMDP& d, int lb, int* bw, cudaStream_t st) {
   return ok();
 }
 
-size_t coarse_lu_smem(int bw) { return (size_t)(bw + 1 + 2 * LU_CHUNK) * (2 * bw + 3) * sizeof(float); }
+size_t coarse_lu_smem(int bw) { return (size_t)(bw + 1 + 2 * LU_CHUNK) * (2 * bw + 2) * sizeof(float); }
 
 int launch_coarse_setup(const DevMDP& d, const int32_t* pi, const PrecondK& p, int bw,
                         const PrecondScratch& w, cudaStream_t st) {

@@ -429,6 +429,7 @@ int server_step(mdp_server_s* s) {
     st.restarts = I.restarts;
     st.sweeps = I.sweeps;
     st.matvecs = I.inner + I.checks;
+    st.breakdowns = I.breakdowns;
     st.residual_inf = I.res;
     const int status = I.status;
     release(s, r, s->ms);

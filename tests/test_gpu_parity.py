@@ -450,3 +450,36 @@ def test_reload_changes_the_window_choice(mg):
         assert st["status"] == 0
         assert rel_err(v, ref.v) <= 1e-6
     h.close()
+
+
+# ------------------------------------------------------------------ lucky breakdown
+@pytest.mark.parametrize("kind", ["dense", "ell"])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_absorbing_mdp_ends_every_inner_solve_by_lucky_breakdown(mg, kind, prec):
+    """Every state absorbing (p_ss(a) = 1): J^pi = (1 - gamma) I, so the first Arnoldi vector
+    spans an invariant Krylov space and the next direction vanishes: Alg. 2's breakdown branch
+    ends each inner solve after one step with the exact least-squares solution.  v is the closed
+    form min_a g(s, a) / (1 - gamma) and pi = argmin_a g(s, a)."""
+    S, A, gamma = 37, 3, 0.95
+    g = np.random.default_rng(4).random((A, S))
+    vdt = np.float64 if prec == "fp64" else np.float32
+    if kind == "dense":
+        h = mg.mdp_create_dense(np.broadcast_to(np.eye(S, dtype=vdt), (A, S, S)).copy(), g, gamma)
+    else:
+        col = np.broadcast_to(np.arange(S, dtype=np.int32)[None, :, None], (A, S, 1)).copy()
+        h = mg.mdp_create_ell(col, np.ones((A, S, 1), dtype=vdt), g, gamma)
+    tol = 1e-12 if prec == "fp64" else 1e-9
+    v, pi, st = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec))
+    assert st["status"] == 0 and st["residual_inf"] <= tol
+    # contraction bound: |v - v*| <= gamma * tol / (1 - gamma)
+    np.testing.assert_allclose(v, g.min(0) / (1 - gamma), rtol=0,
+                               atol=gamma * tol / (1 - gamma) + 1e-13)
+    np.testing.assert_array_equal(pi, g.argmin(0))
+    assert st["outer"] >= 1 and st["breakdowns"] == st["outer"] == st["inner"], st
+    # policy evaluation alone reports the breakdown as informational success
+    ve, ste = mg.policy_eval_gmres(h, g.argmin(0).astype(np.int32), target_inf=1e-10,
+                                   o=mg.opts(precision=prec))
+    assert ste["status"] == 1 and ste["breakdowns"] >= 1, ste
+    # inverse bound: |V - V^pi| <= ||g - J V||_inf / (1 - gamma)
+    np.testing.assert_allclose(ve, g.min(0) / (1 - gamma), rtol=0, atol=1e-10 / (1 - gamma))
+    h.close()

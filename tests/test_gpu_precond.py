@@ -182,3 +182,27 @@ def test_precond_inner_cap_reaches_the_same_fixed_point(mg):
     assert rel_err(v, ref.v) <= 1e-8
     check_policy(pi, oracle.bellman(m, ref.v))
     h.close()
+
+
+# The device's coarse factorization (band build, GTH-form LU in FP32, explicit FP32 inverse)
+# against the oracle's Galerkin J_c inverted in FP64.  Blocks of 128 give a half-bandwidth of at
+# most 8 blocks (the single-thread register LU); blocks of 32 a wider band (the one-warp LU).
+# Bound: 5e-6 of the largest entry, the FP32 GTH form's accuracy in the CPU restatement
+# (tests/test_coarse_factor_cpu.py), at gamma up to 0.9999 where a plain LU would lose it.
+@pytest.mark.parametrize("gamma", [0.999, 0.9999])
+@pytest.mark.parametrize("block,narrow", [(128, True), (32, False)])
+@pytest.mark.parametrize("vdt", [np.float32, np.float64])
+def test_device_coarse_inverse_matches_oracle(mg, gamma, block, narrow, vdt):
+    syn = mdp_synth.ell_banded(3000, 8, 16, 200, 40, gamma, seed=21, val_dtype=vdt)
+    m = oracle.from_synth(syn)
+    pi = oracle.bellman(m, np.zeros(syn.S)).pi
+    _, _, Jc, _ = oracle.two_level(m, pi, block)
+    exact = np.linalg.inv(Jc)
+    h = mg.from_synth(syn)
+    inv, bw = mg.precond_coarse_inverse(h, pi, block)
+    h.close()
+    assert inv.shape == Jc.shape
+    assert (bw <= 8) == narrow, bw
+    rel = float(np.max(np.abs(inv.astype(np.float64) - exact)) / np.max(np.abs(exact)))
+    assert rel <= 5e-6, rel
+    assert float(np.min(inv)) >= -1e-6 * float(np.max(inv))
