@@ -371,6 +371,56 @@ int mdp_server_drain(mdp_server_t s);
 int mdp_server_info(mdp_server_t s, int32_t* active, int32_t* pending, int64_t* bytes_in_use,
                     int64_t* launches);
 
+/* ------------------------------------------------------------ row-sharded solve (multi-GPU)
+ * One MDP whose states are split by rows over several processes, one GPU each: the parallel /
+ * distributed iGMRES-PI the paper names as future work (Sec. 5).  Rank r owns the contiguous
+ * global rows [row_begin[r], row_begin[r+1]) of every P_a and g_a, and the same rows of V, T V,
+ * Phi, pi and of every Krylov vector.  Alg. 2 then needs three exchanges, which the caller
+ * supplies as HOST collectives (any transport: torch.distributed, MPI, NCCL behind a staging
+ * copy): an all-gather of the rows of a vector (V before each Bellman sweep, the Arnoldi vector
+ * before each P^pi matvec, a candidate iterate before its true residual), an allreduce-max
+ * (||Phi||_inf, the true residual's inf-norm, the agreement on each accept / restart decision)
+ * and an allreduce-sum (||Phi||_2^2, the two CGS2 projections Q^T w, ||w||_2^2).  The Hessenberg
+ * least squares and its Givens rotations are replicated on every rank in FP64. */
+typedef struct mdp_shard_s* mdp_shard_t;
+
+/* allgather: local holds this rank's rows (rows * bytes_per_row bytes, host), global receives
+ * every rank's rows in row order (S * bytes_per_row bytes, host).  allreduce: vals[n] (host) is
+ * replaced in place by the sum (op 0) or the maximum (op 1) over ranks; every rank must receive
+ * the same values.  Both return 0 on success; a nonzero return ends the solve with MDP_EDEVICE.
+ * Every rank calls them in the same order with the same sizes. */
+typedef int (*mdp_allgather_fn)(void* ctx, const void* local, void* global, int64_t bytes_per_row);
+typedef int (*mdp_allreduce_fn)(void* ctx, double* vals, int32_t n, int32_t op);
+typedef struct {
+  void* ctx;                  /* passed to the callbacks */
+  int32_t rank, world;        /* this rank, number of ranks */
+  const int64_t* row_begin;   /* [world + 1]: row_begin[0] = 0, row_begin[world] = S */
+  mdp_allgather_fn allgather;
+  mdp_allreduce_fn allreduce;
+} mdp_comm;
+
+/* This rank's rows of an ELL MDP with S states in all: rows [row0, row0 + rows), arrays in the
+ * layout of mdp_create_ell restricted to those rows: col / val [A][rows][k] (int32 global
+ * column indices in [0, S); FP32 or FP64 values), g [A][rows] (FP64), host pointers, copied.
+ * Every action is allowed.  Validation on the host: sizes, 0 <= col < S, values finite and
+ * >= 0, row sums within 1e-5 of 1, g finite, 0 < gamma < 1 (MDP_EINVAL otherwise). */
+int mdp_shard_create(int64_t S, int64_t row0, int64_t rows, int32_t A, int32_t k, const int32_t* col,
+                     const void* val, int val_dtype, const double* g, double gamma,
+                     mdp_shard_t* out);
+void mdp_shard_destroy(mdp_shard_t h);
+
+/* iGMRES-PI (Alg. 2) on the sharded MDP, called by every rank with its own shard and the same
+ * options: the stopping rules of ipi_solve (outer ||T V - V||_inf <= tol; inner true residual
+ * ||g^pi - J^pi V||_inf <= alpha_k ||Phi_k||_inf, formed once the Givens estimate comes within
+ * sqrt(S) of it, at the end of each restart cycle, at a lucky breakdown and at max_inner), in
+ * FP64 arithmetic (opts->precision is ignored; precond_block must be 0).  Outputs are this rank's
+ * rows: v_out[rows] = T(V_K), pi_out[rows] = GreedyPolicy(V_K) (host or device pointers, pi_out
+ * may be NULL).  opts->v0 (rows entries) warm-starts V.  Returns MDP_OK, MDP_ENOCONV at
+ * max_outer, MDP_EINVAL when the communicator's partition does not match the shard, MDP_EDEVICE
+ * on a CUDA or callback failure. */
+int ipi_solve_sharded(mdp_shard_t h, const mdp_comm* comm, const mdp_opts* opts, double* v_out,
+                      int32_t* pi_out, mdp_stats* stats);
+
 /* Inspection of the two-level preconditioner (the preconditioned policy evaluation that
  * ipi_solve runs with mdp_opts.precond_block; preconditioning is named as future work in
  * Sec. 5).  For the policy pi[S] (host or device pointer, every entry an allowed action) and

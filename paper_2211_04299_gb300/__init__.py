@@ -444,3 +444,120 @@ def precond_coarse_inverse(h: MDPHandle, pi, block: int):
     _check(lib().mdp_precond_coarse_inverse(h.ptr, _ptr(pi), int(block), _ptr(inv), C.byref(nc),
                                             C.byref(bw)), "mdp_precond_coarse_inverse")
     return inv, bw.value
+
+
+# ---------------------------------------------------------------- row-sharded solve
+def row_partition(S: int, world: int) -> np.ndarray:
+    """Contiguous, balanced row blocks: row_begin[r] = floor(r * S / world), [world + 1]."""
+    return np.array([(r * S) // world for r in range(world + 1)], dtype=np.int64)
+
+
+class ShardComm:
+    """Host collectives of ipi_solve_sharded over a torch.distributed process group (CPU
+    tensors: gloo; for an NCCL job pass a gloo group made with torch.distributed.new_group).
+    Every rank of the group builds one with the same row partition."""
+
+    def __init__(self, row_begin, group=None):
+        import torch.distributed as dist
+        self.dist = dist
+        self.group = group
+        self.rank = dist.get_rank(group)
+        self.world = dist.get_world_size(group)
+        self.row_begin = np.ascontiguousarray(row_begin, dtype=np.int64)
+        if self.row_begin.shape != (self.world + 1,):
+            raise ValueError("row_begin must have world + 1 entries")
+        self._ag = _lib.ALLGATHER_FN(self._allgather)
+        self._ar = _lib.ALLREDUCE_FN(self._allreduce)
+        self.c = _lib.mdp_comm(None, self.rank, self.world,
+                               self.row_begin.ctypes.data_as(C.POINTER(C.c_int64)),
+                               self._ag, self._ar)
+
+    def allgather(self, local: np.ndarray, bytes_per_row: int) -> np.ndarray:
+        """Every rank's rows (raw bytes, this rank's in `local`) in row order."""
+        import torch
+        rb = self.row_begin
+        counts = np.diff(rb) * bytes_per_row
+        buf = np.zeros(int(counts.max()), dtype=np.uint8)
+        buf[:counts[self.rank]] = np.frombuffer(local, dtype=np.uint8, count=int(counts[self.rank]))
+        t = torch.from_numpy(buf)
+        outs = [torch.empty_like(t) for _ in range(self.world)]
+        self.dist.all_gather(outs, t, group=self.group)
+        return np.concatenate([o.numpy()[:counts[r]] for r, o in enumerate(outs)])
+
+    def allreduce(self, vals: np.ndarray, op: int) -> np.ndarray:
+        import torch
+        t = torch.from_numpy(np.array(vals, dtype=np.float64))
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX if op == 1 else self.dist.ReduceOp.SUM,
+                             group=self.group)
+        return t.numpy()
+
+    # ctypes entry points (must not raise into C)
+    def _allgather(self, ctx, local, glob, bytes_per_row):
+        try:
+            rows = int(self.row_begin[self.rank + 1] - self.row_begin[self.rank])
+            src = (C.c_uint8 * (rows * bytes_per_row)).from_address(local)
+            out = self.allgather(bytes(src), int(bytes_per_row))
+            C.memmove(glob, out.ctypes.data, out.nbytes)
+            return 0
+        except Exception:
+            return -1
+
+    def _allreduce(self, ctx, vals, n, op):
+        try:
+            arr = np.ctypeslib.as_array(vals, shape=(n,))
+            arr[:] = self.allreduce(arr, op)
+            return 0
+        except Exception:
+            return -1
+
+
+class ShardHandle:
+    """Owns an mdp_shard_t: this rank's rows of a row-sharded ELL MDP."""
+
+    def __init__(self, ptr, S, row0, rows, A, k):
+        self._p = ptr
+        self.S, self.row0, self.rows, self.A, self.k = S, row0, rows, A, k
+
+    @property
+    def ptr(self):
+        if self._p is None:
+            raise ValueError("shard is closed")
+        return self._p
+
+    def close(self):
+        if self._p is not None:
+            lib().mdp_shard_destroy(self._p)
+            self._p = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def mdp_shard_create(S: int, row0: int, col, val, g, gamma: float) -> ShardHandle:
+    """col / val [A, rows, k] (global int32 columns; float32 or float64), g [A, rows] float64:
+    rows [row0, row0 + rows) of an ELL MDP with S states."""
+    A, rows, k = val.shape
+    col = np.ascontiguousarray(col, dtype=np.int32)
+    val = np.ascontiguousarray(val)
+    g = np.ascontiguousarray(g, dtype=np.float64)
+    if col.shape != (A, rows, k) or g.shape != (A, rows):
+        raise ValueError("col/val must be (A, rows, k) and g (A, rows)")
+    h = C.c_void_p()
+    _check(lib().mdp_shard_create(int(S), int(row0), int(rows), A, k, _ptr(col), _ptr(val),
+                                  _dtype_code(val), _ptr(g), float(gamma), C.byref(h)),
+           "mdp_shard_create")
+    return ShardHandle(h, int(S), int(row0), int(rows), A, k)
+
+
+def ipi_solve_sharded(h: ShardHandle, comm: ShardComm, o=None):
+    """iGMRES-PI on the row-sharded MDP -> this rank's (v = T(V_K), pi, stats)."""
+    o = o or opts()
+    v = np.empty(h.rows, dtype=np.float64)
+    pi = np.empty(h.rows, dtype=np.int32)
+    st = mdp_stats()
+    _check(lib().ipi_solve_sharded(h.ptr, C.byref(comm.c), C.byref(o), _ptr(v), _ptr(pi),
+                                   C.byref(st)), "ipi_solve_sharded")
+    return v, pi, st.as_dict()

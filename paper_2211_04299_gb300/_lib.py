@@ -45,6 +45,17 @@ class mdp_stats(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+# host collectives of the row-sharded solve (include/mdpgpu.h: mdp_allgather_fn, mdp_allreduce_fn)
+ALLGATHER_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64)
+ALLREDUCE_FN = C.CFUNCTYPE(C.c_int, C.c_void_p, C.POINTER(C.c_double), C.c_int32, C.c_int32)
+
+
+class mdp_comm(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("rank", C.c_int32), ("world", C.c_int32),
+                ("row_begin", C.POINTER(C.c_int64)), ("allgather", ALLGATHER_FN),
+                ("allreduce", ALLREDUCE_FN)]
+
+
 _vp = C.c_void_p
 _dp = C.POINTER(C.c_double)
 _ip = C.POINTER(C.c_int32)
@@ -53,6 +64,9 @@ _h = C.c_void_p
 # name -> (restype, argtypes); every symbol include/mdpgpu.h declares
 SIGNATURES = {
     "mdp_precond_coarse_inverse": (C.c_int, [_h, _vp, C.c_int32, _vp, C.POINTER(C.c_int64), _ip]),
+    "mdp_shard_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _vp, _vp, C.c_int, _vp, C.c_double, C.POINTER(_h)]),
+    "mdp_shard_destroy": (None, [_h]),
+    "ipi_solve_sharded": (C.c_int, [_h, C.POINTER(mdp_comm), C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
     "mdp_probe_alu": (C.c_int, [C.c_int32, _dp]),
     "mdp_create_dense": (C.c_int, [C.c_int64, C.c_int32, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),
     "mdp_create_ell": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),

@@ -13,6 +13,7 @@ HEADER = os.path.join(ROOT, "include", "mdpgpu.h")
 def header_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    text = re.sub(r"^\s*typedef[^;]*;", "", text, flags=re.M)  # callback types are not entry points
     names = re.findall(r"^\s*(?:const\s+)?[\w\s\*]+?\b(\w+)\s*\(", text, flags=re.M)
     return sorted({n for n in names if n not in ("if", "while", "for", "return", "sizeof")})
 
