@@ -73,6 +73,9 @@ def parse():
     ap.add_argument("--study", choices=["fig2"], default=None,
                     help="fig2: GMRES vs VI policy evaluation across gamma at n=100 (Sec. 3.1): "
                          "Arnoldi steps, VI sweeps and times on the GPU; one JSON line")
+    ap.add_argument("--sweep-only", action="store_true",
+                    help="time Bellman sweeps alone (bellman_apply at a fixed v, no solve) on the "
+                         "single-MDP workloads: the metric's Bellman-op HBM GB/s")
     ap.add_argument("--no-tune", action="store_true",
                     help="batched workload: keep the library's lanes per row (no autotuning), "
                          "so the launch sequence is the same on every run (for profilers)")
@@ -883,6 +886,8 @@ def main():
     S, A = syn.S, syn.A
     h = mg.from_synth(syn)
     stream = torch.cuda.Stream()  # not the legacy default stream: see run_batch_bench
+    if args.sweep_only:
+        return run_sweep_bench(args, mg, torch, syn, h, stream, world, rank, local)
     torch.cuda.set_stream(stream)
     h.set_stream(stream)
     o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision="mixed", forcing_c=args.forcing_c,
@@ -1079,6 +1084,57 @@ def main():
     return 0
 
 
+def run_sweep_bench(args, mg, torch, syn, h, stream, world, rank, local):
+    """Bellman sweeps alone: bellman_apply (mixed arithmetic) at a fixed v, outputs pi and T v
+    on the device, no solve around it (so the L2 holds nothing of a Krylov basis)."""
+    torch.cuda.set_stream(stream)
+    h.set_stream(stream)
+    v = torch.from_numpy(np.random.default_rng(7).uniform(0.0, 100.0, syn.S)).cuda()
+    Tv = torch.empty(syn.S, dtype=torch.float64, device="cuda")
+    pi = torch.empty(syn.S, dtype=torch.int32, device="cuda")
+    lib = mg.lib()
+    import ctypes as C
+
+    def call():
+        rc = lib.bellman_apply_dev(h.ptr, C.c_void_p(v.data_ptr()), C.c_void_p(Tv.data_ptr()),
+                                   C.c_void_p(pi.data_ptr()), None, None, mg.MDP_PREC_MIXED)
+        assert rc == 0
+
+    for _ in range(max(3, args.warmup)):
+        call()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    clocks.start()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    ev[0].record(stream)
+    for i in range(args.steps):
+        call()
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    mean_ms = ev[0].elapsed_time(ev[-1]) / args.steps
+    # the sweep writes pi and T v (12 B per state) instead of pi, T v and Phi (16 B)
+    sb = sweep_algorithmic_bytes(syn) - 4 * syn.S
+    gbs = sb / (mean_ms * 1e-3) / 1e9
+    peak, kind = peaks()
+    line = {"metric": "Bellman-op HBM GB/s", "value": job_rate(sb / 1e9, mean_ms / 1e3, world),
+            "unit": "GB/s", "n_gpus": world, "steps": args.steps, "warmup": max(3, args.warmup),
+            "ms_per_step": mean_ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "mixed: f32 P, double-float (2xf32) sums",
+            "data": "synthetic", "step": "one bellman_apply call (v conversion + fused sweep)",
+            "config": dict(config_fields(args, syn), parallelism=f"replicas x{world}"),
+            "latency_ms": {"p50": float(np.percentile(ms, 50)), "p99": float(np.percentile(ms, 99))},
+            "roofline": {"bound": "hbm", "kernel": sweep_kernel_name(syn), "achieved": gbs,
+                         "peak": peak, "unit": "GB/s", "frac": gbs / peak, "peak_source": kind,
+                         "traffic": None, "algorithmic_bytes": sb},
+            "gpu_launches": 2 * args.steps, "clocks": clk}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    h.close()
+    return 0
+
+
 def fp64_plain_leg(args, mg, torch, syn, stream, v_out, pi_out, n64=10):
     import mdp_synth
     S, A = syn.S, syn.A
@@ -1173,7 +1229,8 @@ def banded_leg(args, mg, torch, stream):
         if name == "plain":
             out["bellman_sweep"] = {"kernel": sweep_kernel_name(syn), "ms": sweep_ms, "gbs": gbs,
                                     "algorithmic_bytes": sweep_algorithmic_bytes(syn),
-                                    "frac": gbs / peak, "peak": peak, "peak_source": kind}
+                                    "frac": gbs / peak, "peak": peak, "peak_source": kind,
+                                    "traffic": traffic_for("sweep_ell_window_cfg3")}
     h.close()
     return out
 
