@@ -678,7 +678,9 @@ def replay(trace, npool, submit, poll, idle_wait=0.0002):
     return lat, t_end - (t0 + trace[0]["t"])
 
 
-def run_serve_bench(args, mg, torch, dist, world, rank, local):
+def run_serve_bench(args, mg, torch, dist, world, rank, local, extra=False):
+    """The serving workload.  extra=True: the leg reported beside the headline line (a shorter
+    trace, no CPU leg); returns the dict instead of printing it."""
     import mdp_synth
     trace, npool = serve_trace(args)
     n = len(trace)
@@ -800,6 +802,10 @@ def run_serve_bench(args, mg, torch, dist, world, rank, local):
         for h, _ in hs64:
             h.close()
 
+    if extra:
+        for key in ("metric", "n_gpus", "higher_is_better", "scaling", "vs_baseline", "data"):
+            line.pop(key, None)
+        return line
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         import oracle
         t_tot, m_done = 0.0, 0
@@ -1075,6 +1081,11 @@ def main():
         line["config4_batched"] = run_batch_bench(args, mg, torch, dist, world, rank, local,
                                                   extra=True)
         line["config3_banded"] = banded_leg(args, mg, torch, stream)
+        line["config1_small"] = small_leg(args, mg, torch, stream)
+        serve_args = argparse.Namespace(**vars(args))
+        serve_args.duration = 10.0
+        line["config5_served"] = run_serve_bench(serve_args, mg, torch, dist, world, rank, local,
+                                                 extra=True)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if h is not None:
@@ -1187,6 +1198,42 @@ def fp64_plain_leg(args, mg, torch, syn, stream, v_out, pi_out, n64=10):
                          "peak_source": "measured FP64 FMA rate (mdp_probe_alu, this run)",
                          "hbm_frac": (bytes64 / (sweep_ms * 1e-3) / 1e9) / hbm_peak
                          if sweep_ms > 0 else None}}
+
+
+def small_leg(args, mg, torch, stream, n=20):
+    """Config 1 (S = 2000, A = 5, k = 16, gamma = 0.95, FP64 values): the plain FP64 form of
+    Alg. 2 as the configuration states it, and the mixed form on the same values rounded to FP32;
+    the whole problem lives in L2, so this measures latency, not bandwidth."""
+    import mdp_synth
+    syn = mdp_synth.config(1)
+    out = {"workload": "ELL S=2000, A=5, k=16, gamma=0.95, alpha=0.1, W=30, tol 1e-8", "solves": n}
+    for name, prec, data in (("fp64_plain", "fp64", syn.val),
+                             ("mixed", "mixed", syn.val.astype(np.float32))):
+        h = mg.from_synth(mdp_synth.SynthMDP(S=syn.S, A=syn.A, gamma=syn.gamma, g=syn.g,
+                                             kind="ell", col=syn.col, val=data))
+        h.set_stream(stream)
+        o = mg.opts(tol=TOL, alpha=ALPHA, restart=W_, precision=prec)
+        vo = torch.empty(syn.S, dtype=torch.float64, device="cuda")
+        po = torch.empty(syn.S, dtype=torch.int32, device="cuda")
+        for _ in range(3):
+            mg.ipi_solve(h, o, v_out=vo, pi_out=po)
+        torch.cuda.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(n + 1)]
+        ev[0].record(stream)
+        sts = []
+        for i in range(n):
+            _, _, st = mg.ipi_solve(h, o, v_out=vo, pi_out=po)
+            ev[i + 1].record(stream)
+            sts.append(st)
+        torch.cuda.synchronize()
+        step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(n)]
+        out[name] = {"value": n / (ev[0].elapsed_time(ev[-1]) / 1000.0), "unit": "solves/s",
+                     "latency_ms": {"p50": float(np.percentile(step_ms, 50)),
+                                    "p99": float(np.percentile(step_ms, 99))},
+                     "outer": sts[-1]["outer"], "inner": sts[-1]["inner"],
+                     "converged": all(x["status"] == 0 and x["residual_inf"] <= TOL for x in sts)}
+        h.close()
+    return out
 
 
 def banded_leg(args, mg, torch, stream):

@@ -444,6 +444,16 @@ int mdp_precond_coarse_inverse(mdp_t h, const int32_t* pi, int32_t block, float*
  * failures. */
 int mdp_probe_alu(int32_t dtype, double* tflops);
 
+/* Self-test of the bounded device waits (no counterpart in the paper).  Every spin-wait in the
+ * library's kernels (the mbarrier waits of the bulk-copy pipelines) gives up after about a
+ * second of SM clock cycles, raises an error flag that the host reads back as MDP_ETIMEOUT, and
+ * leaves the context usable.  This call runs that same wait helper in a one-thread kernel on the
+ * current device, on an mbarrier that expects one arrival, with the given limit in clock cycles
+ * (1 .. 2^31): with arrive = 0 nothing arrives, so the wait runs out and the call returns
+ * MDP_ETIMEOUT; with arrive = 1 the thread arrives first and the call returns MDP_OK.  No copy
+ * is in flight while it waits.  Synchronous; allocates 4 bytes for the flag. */
+int mdp_selftest_wait(int64_t limit_cycles, int32_t arrive);
+
 /* Message for the last nonzero return on this thread ("" if none). */
 const char* mdp_last_error(void);
 

@@ -67,6 +67,7 @@ SIGNATURES = {
     "mdp_shard_create": (C.c_int, [C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_int32, _vp, _vp, C.c_int, _vp, C.c_double, C.POINTER(_h)]),
     "mdp_shard_destroy": (None, [_h]),
     "ipi_solve_sharded": (C.c_int, [_h, C.POINTER(mdp_comm), C.POINTER(mdp_opts), _vp, _vp, C.POINTER(mdp_stats)]),
+    "mdp_selftest_wait": (C.c_int, [C.c_int64, C.c_int32]),
     "mdp_probe_alu": (C.c_int, [C.c_int32, _dp]),
     "mdp_create_dense": (C.c_int, [C.c_int64, C.c_int32, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),
     "mdp_create_ell": (C.c_int, [C.c_int64, C.c_int32, C.c_int32, _vp, _vp, C.c_int, _vp, C.c_double, _vp, C.POINTER(_h)]),

@@ -252,11 +252,13 @@ __device__ __forceinline__ bool mbar_test(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err) {
+constexpr long long MBAR_WAIT_CYCLES = 1LL << 31;  // about one second at the SM clock
+__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity, int* err,
+                                          long long limit = MBAR_WAIT_CYCLES) {
   if (mbar_test(b, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_test(b, parity)) {
-    if (clock64() - t0 > (1LL << 31)) {
+    if (clock64() - t0 > limit) {
       if (err) atomicExch(err, 1);
       return false;
     }

@@ -237,8 +237,10 @@ __global__ void __launch_bounds__(32) coarse_lu_kernel(float* band, int nc, int 
   cp_async_wait0();
 }
 
-// Reciprocal without branches: the approximate hardware reciprocal and one Newton step
-// (x' = x + x (1 - u x)), within an ulp or two, which is all the coarse factors need.
+// Reciprocal without branches: the approximate hardware reciprocal refined by one Newton-Raphson
+// step x' = x + x (1 - u x), which roughly doubles its number of correct bits.  The factors it
+// feeds are checked as a whole: the device's J_c^{-1} against the oracle's FP64 inverse of the
+// Galerkin operator, within 5e-6 of its largest entry up to gamma = 0.9999 (GPU test).
 __device__ __forceinline__ float rcp_nr(float u) {
   float x;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(x) : "f"(u));

@@ -1,4 +1,5 @@
-// Arithmetic-rate probe: mdp_probe_alu.
+// Diagnostics: the arithmetic-rate probe mdp_probe_alu and the bounded-wait self-test
+// mdp_selftest_wait.
 //
 // The plain FP64 form of the solver accumulates every transition entry with an FP64 FMA, and
 // GB300's FP64 pipe is a small fraction of its FP32 pipe, so that form's Bellman sweep can be
@@ -71,7 +72,34 @@ int probe(int iters, double* tflops) {
   return r;
 }
 
+// One thread waits, through the pipelines' bounded-wait helper, on an mbarrier that expects one
+// arrival; with arrive = 0 nothing arrives (and no copy is in flight), so the wait runs out after
+// `limit` clock cycles and raises the error flag; with arrive = 1 the thread arrives first.
+__global__ void wait_selftest_kernel(long long limit, int arrive, int* err) {
+  __shared__ __align__(8) uint64_t bar;
+  mdp::mbar_init(&bar, 1);
+  mdp::mbar_fence_init();
+  if (arrive) mdp::mbar_arrive(&bar);
+  mdp::mbar_wait(&bar, 0, err, limit);
+}
+
 }  // namespace
+
+extern "C" int mdp_selftest_wait(int64_t limit_cycles, int32_t arrive) {
+  if (limit_cycles < 1 || limit_cycles > mdp::MBAR_WAIT_CYCLES || (arrive != 0 && arrive != 1))
+    return mdp::set_error(MDP_EINVAL, "mdp_selftest_wait: limit must lie in [1, 2^31], arrive 0 or 1");
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess)
+    return mdp::set_error(MDP_ENOMEM, "mdp_selftest_wait: cudaMalloc failed");
+  int h = 0;
+  cudaMemset(err, 0, sizeof(int));
+  wait_selftest_kernel<<<1, 1>>>((long long)limit_cycles, arrive, err);
+  const cudaError_t e = cudaMemcpy(&h, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(err);
+  if (e != cudaSuccess || cudaGetLastError() != cudaSuccess)
+    return mdp::set_error(MDP_EDEVICE, "mdp_selftest_wait: launch failed");
+  return h ? mdp::set_error(MDP_ETIMEOUT, "bounded device wait ran out (self-test)") : MDP_OK;
+}
 
 extern "C" int mdp_probe_alu(int32_t dtype, double* tflops) {
   if (!tflops) return mdp::set_error(MDP_EINVAL, "mdp_probe_alu: null output");

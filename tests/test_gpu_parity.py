@@ -483,3 +483,24 @@ def test_absorbing_mdp_ends_every_inner_solve_by_lucky_breakdown(mg, kind, prec)
     # inverse bound: |V - V^pi| <= ||g - J V||_inf / (1 - gamma)
     np.testing.assert_allclose(ve, g.min(0) / (1 - gamma), rtol=0, atol=1e-10 / (1 - gamma))
     h.close()
+
+
+# ------------------------------------------------------------------ bounded device waits
+def test_bounded_wait_runs_out_and_the_context_stays_usable(mg):
+    """A wait on an mbarrier that nothing completes, with a host-set limit of 2^20 cycles
+    (about half a millisecond), returns MDP_ETIMEOUT through the same helper the bulk-copy
+    pipelines use; the same wait with the arrival done returns MDP_OK; afterwards a dense sweep
+    through the bulk-copy pipeline still matches the oracle."""
+    lib = mg.lib()
+    assert lib.mdp_selftest_wait(1 << 20, 0) == -5          # MDP_ETIMEOUT
+    assert b"ran out" in lib.mdp_last_error()
+    assert lib.mdp_selftest_wait(1 << 20, 1) == 0
+    assert lib.mdp_selftest_wait(0, 0) == -1                # limit out of range: MDP_EINVAL
+    syn = mdp_synth.dense_dirichlet(1200, 4, 0.1, 0.99, seed=3, dtype=np.float32)
+    h = mg.from_synth(syn)
+    v = np.random.default_rng(0).normal(size=syn.S) * 10
+    sw = oracle.bellman(oracle.from_synth(syn), v)
+    Tv, pi, res = mg.bellman_apply(h, v, precision="mixed")
+    assert rel_err(Tv, sw.Tv) <= 1e-12
+    check_policy(pi, sw)
+    h.close()
