@@ -93,6 +93,53 @@ __device__ __forceinline__ dfl shfl_xor_df(dfl x, int off) {
   return {__shfl_xor_sync(0xffffffffu, x.hi, off), __shfl_xor_sync(0xffffffffu, x.lo, off)};
 }
 
+// Packed pairs of FP32 values in one 64-bit register and the paired FP32 instructions of this
+// architecture (add / sub / mul / fma .rn.f32x2: two IEEE round-to-nearest operations per
+// instruction, never contracted), so two independent error-free transforms issue as one.
+typedef unsigned long long f2x;
+__device__ __forceinline__ f2x f2_pack(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(f2x x, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(x));
+}
+__device__ __forceinline__ f2x f2_add(f2x a, f2x b) {
+  f2x r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x f2_sub(f2x a, f2x b) {
+  f2x r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x f2_mul(f2x a, f2x b) {
+  f2x r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x f2_fma(f2x a, f2x b, f2x c) {
+  f2x r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+// Two running sums, each of products p * (vh + vl), in the manner of AccDF below but on packed
+// pairs: with nvh = -vh (exact), the product's high part is -(p * nvh) and its error
+// fma(p, vh, p * nvh); TwoSum of the high parts is written with the negated term, so every step is
+// exact as in the scalar form.  sh holds the two high sums, sl their error terms.
+__device__ __forceinline__ void f2_acc(f2x& sh, f2x& sl, f2x p, f2x vh, f2x nvh, f2x vl) {
+  const f2x nph = f2_mul(p, nvh);          // -(p * vh) rounded
+  const f2x pe = f2_fma(p, vh, nph);       // exact error of the product
+  const f2x s = f2_sub(sh, nph);           // sh + p * vh rounded
+  const f2x bb = f2_sub(s, sh);
+  const f2x t2 = f2_sub(sh, f2_sub(s, bb));
+  const f2x e = f2_sub(t2, f2_add(nph, bb));  // TwoSum error: (sh - (s - bb)) + (ph - bb)
+  sl = f2_add(sl, f2_add(e, f2_fma(p, vl, pe)));
+  sh = s;
+}
+
 // Running sum of products p * v with p FP32 and v double-float, accurate to about 2^-48
 // relative: each product is split exactly (TwoProduct), the high parts are added with
 // TwoSum and every error term goes to a low word; every 32 terms the chunk is folded into

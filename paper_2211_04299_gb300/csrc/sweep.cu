@@ -563,10 +563,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
     }
   } else {
     // ---------------- consumers
-    // Per row a (hi, lo) pair: the hi part gathers the high halves of the exact products
-    // p*vh with TwoSum, every error term (product error, p*vl, TwoSum error) goes to lo.
-    // A thread adds 2 terms per stage and row, so up to 16 stages the lo word holds at most
-    // 32 error terms; beyond that the pair is folded into a double-word total.
+    // Per row two (hi, lo) pairs, for the even and the odd column of the thread, held as packed
+    // FP32 pairs (f2_acc): the hi parts gather the high halves of the exact products p*vh with
+    // TwoSum, every error term (product error, p*vl, TwoSum error) goes to lo.  Each pair adds
+    // one term per stage and row, so up to 16 stages a lo word holds at most 16 error terms;
+    // then the pairs are folded into a double-word total.
     const int t = threadIdx.x;  // 0..511
     const int col = 2 * t;
     const int ldi = (int)ld;
@@ -576,12 +577,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
     uint32_t ph = 0;
     float4 vnext = col < ldi ? __ldg(vq + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     for (int64_t s = blockIdx.x; s < d.S && ok; s += gridDim.x, ++ri) {
-      float sh[R], sl[R];
+      f2x sh[R], sl[R];
       dfl tot[R];
 #pragma unroll
-      for (int g = 0; g < R; ++g) { sh[g] = 0.f; sl[g] = 0.f; tot[g] = {0.f, 0.f}; }
+      for (int g = 0; g < R; ++g) { sh[g] = 0ull; sl[g] = 0ull; tot[g] = {0.f, 0.f}; }
       for (int c0 = 0, ch = 0; c0 < ldi; c0 += TS_CW, ++ch) {
-        const float4 vv = vnext;
+        const float4 vv = vnext;  // (hi, lo) of columns col and col + 1
         {  // the v entries of the next stage (wrapping to the next state's first chunk)
           const int cn = (c0 + TS_CW < ldi) ? c0 + TS_CW : 0;
           vnext = (cn + col < ldi) ? __ldg(vq + ((cn + col) >> 1)) : make_float4(0.f, 0.f, 0.f, 0.f);
@@ -590,21 +591,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
         const unsigned char* sg = stg + (size_t)st * L.stage_bytes;
         if (col < ldi - c0) {
           const float* pp = reinterpret_cast<const float*>(sg) + col;
+          const f2x vh = f2_pack(vv.x, vv.z), vl = f2_pack(vv.y, vv.w);
+          const f2x nvh = f2_pack(-vv.x, -vv.z);
 #pragma unroll
           for (int g = 0; g < R; ++g) {
-            const float2 pv = *reinterpret_cast<const float2*>(pp + g * TS_CW);
-            // term 1: p = pv.x, v = (vv.x, vv.y)
-            float prh = __fmul_rn(pv.x, vv.x);
-            float pre = __fmaf_rn(pv.x, vv.x, -prh);
-            dfl a = two_sum(sh[g], prh);
-            float lo = __fadd_rn(a.lo, __fmaf_rn(pv.x, vv.y, pre));
-            // term 2: p = pv.y, v = (vv.z, vv.w)
-            prh = __fmul_rn(pv.y, vv.z);
-            pre = __fmaf_rn(pv.y, vv.z, -prh);
-            dfl b = two_sum(a.hi, prh);
-            lo = __fadd_rn(lo, __fadd_rn(b.lo, __fmaf_rn(pv.y, vv.w, pre)));
-            sh[g] = b.hi;
-            sl[g] = __fadd_rn(sl[g], lo);
+            const f2x pv = *reinterpret_cast<const f2x*>(pp + g * TS_CW);  // p of both columns
+            f2_acc(sh[g], sl[g], pv, vh, nvh, vl);
           }
         }
         __syncwarp();
@@ -613,9 +605,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
         if ((ch & 15) == 15) {
 #pragma unroll
           for (int g = 0; g < R; ++g) {
-            tot[g] = df_add(tot[g], two_sum(sh[g], sl[g]));
-            sh[g] = 0.f;
-            sl[g] = 0.f;
+            float h0, h1, l0, l1;
+            f2_unpack(sh[g], h0, h1);
+            f2_unpack(sl[g], l0, l1);
+            tot[g] = df_add(tot[g], df_add(two_sum(h0, l0), two_sum(h1, l1)));
+            sh[g] = 0ull;
+            sl[g] = 0ull;
           }
         }
       }
@@ -625,7 +620,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
 #pragma unroll
       for (int g = 0; g < TS_RMAX; ++g) {
         if (g < R) {
-          parts[g] = two_sum(sh[g], sl[g]);
+          float h0, h1, l0, l1;
+          f2_unpack(sh[g], h0, h1);
+          f2_unpack(sl[g], l0, l1);
+          parts[g] = df_add(two_sum(h0, l0), two_sum(h1, l1));
           if (folded) parts[g] = df_add(tot[g], parts[g]);
         } else {
           parts[g] = {0.f, 0.f};
