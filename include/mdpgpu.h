@@ -146,6 +146,13 @@ typedef struct {
  * global-gather kernels instead (same values; for comparison and profiling).  mdp_set_geometry
  * with sweep_blocks > 0 (matvec_blocks > 0) also selects the global-gather sweep (matvec). */
 #define MDP_FLAG_NO_WINDOW 2
+/* With precond_block > 0, ipi_solve builds the coarse factorization of the two-level
+ * preconditioner for the first policy and rebuilds it only when more than 1 in 1000 states have
+ * changed their action since it was built (a preconditioner built for a nearby policy is still a
+ * valid right preconditioner: the iterate uses the same M^{-1} as the Arnoldi process, so only
+ * the number of steps can change, never the result).  MDP_FLAG_PC_REBUILD rebuilds it for every
+ * policy. */
+#define MDP_FLAG_PC_REBUILD 4
 
 /* alpha 0.1, tol 1e-8, restart 30, max_outer 100, max_inner 3000, precision MIXED,
  * opi_W 50, pi_inner_tol_exp 13, flags 0, v0 NULL, forcing_c 0, precond_block 0. */

@@ -13,6 +13,7 @@ import numpy as np
 
 from . import _lib
 from ._lib import (MDP_F32, MDP_F64, MDP_FLAG_HOST_LOOP, MDP_FLAG_NO_WINDOW, MDP_PREC_FP64,  # noqa: F401
+                   MDP_FLAG_PC_REBUILD,
                    MDP_PREC_MIXED, MDPError, mdp_opts, mdp_server_opts, mdp_stats)
 
 __all__ = [

@@ -15,6 +15,7 @@ MDP_F32, MDP_F64 = 0, 1
 MDP_PREC_FP64, MDP_PREC_MIXED = 0, 1
 MDP_FLAG_HOST_LOOP = 1
 MDP_FLAG_NO_WINDOW = 2
+MDP_FLAG_PC_REBUILD = 4
 
 STATUS_NAMES = {0: "ok", -1: "einval", -2: "enomem", -3: "enoconv", -4: "edevice",
                 -5: "etimeout", 1: "breakdown"}

@@ -110,6 +110,10 @@ struct mdp_s {
     void* ec = nullptr;
     void* z = nullptr;
     float* f = nullptr;
+    int32_t* pi_built = nullptr;  // the policy the current coarse factors were built for
+    int* nchanged = nullptr;      // states whose action differs from pi_built (device)
+    int* h_nchanged = nullptr;    // pinned copy
+    int built = 0;                // factors valid for the current solve
     int* bwbuf = nullptr;
     size_t bytes = 0;
   } pc;
@@ -146,9 +150,10 @@ void free_ws(Workspace& w) {
 }
 
 void free_pc(mdp_s::Precond& p) {
-  void* ptrs[] = {p.band, p.cl, p.cu, p.dinv, p.inv, p.E, p.ec, p.z, p.f};
+  void* ptrs[] = {p.band, p.cl, p.cu, p.dinv, p.inv, p.E, p.ec, p.z, p.f, p.pi_built, p.nchanged};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  if (p.h_nchanged) cudaFreeHost(p.h_nchanged);
   int* keep = p.bwbuf;
   const int bl = p.bw_lb, bc = p.bw_cached;
   p = mdp_s::Precond{};
@@ -295,6 +300,12 @@ int ensure_pc(mdp_t h, int kt, int W, int lb) {
   RK(alloc0(&p.ec, (size_t)p.ldc * ek, acc));
   RK(alloc0(&p.z, (size_t)h->ws.ldq * ek, acc));
   RK(alloc0((void**)&p.f, (size_t)p.ldc * 4, acc));
+  RK(alloc0((void**)&p.pi_built, (size_t)S * 4, acc));
+  RK(alloc0((void**)&p.nchanged, 64, acc));
+  if (cudaMallocHost((void**)&p.h_nchanged, 64) != cudaSuccess) {
+    p.h_nchanged = nullptr;
+    return fail(MDP_ENOMEM, "cudaMallocHost failed");
+  }
   return MDP_OK;
 }
 
@@ -757,6 +768,7 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
   if (o.precond_block) {
     RK(ensure_pc(h, arith, o.restart, log2_exact(o.precond_block)));
     h->pc_on = 1;
+    h->pc.built = 0;
   }
   RK(load_v(h, o.v0, arith));
   int status = MDP_ENOCONV;
@@ -769,10 +781,24 @@ int run_ipi(mdp_t h, const mdp_opts& o, double* v_out, int32_t* pi_out, mdp_stat
     if (k >= o.max_outer) break;
     const double thr = inexact_threshold(o.alpha, o.forcing_c, so.res_inf, h->thr_floor);
     const bool host_loop = (o.flags & MDP_FLAG_HOST_LOOP) != 0;
-    if (h->pc_on) {  // coarse operator of the new policy pi_k: band, LU, explicit inverse
-      RK(launch_coarse_setup(h->d, w.pi, pck(h), h->pc.bw,
-                             PrecondScratch{h->pc.band, h->pc.cl, h->pc.cu, h->pc.dinv}, h->stream));
-      h->launches += 4;
+    if (h->pc_on) {  // coarse operator of the policy pi_k: band, LU, explicit inverse
+      auto& pc = h->pc;
+      bool rebuild = !pc.built || (o.flags & MDP_FLAG_PC_REBUILD);
+      if (!rebuild) {  // factors of a nearby policy remain a valid right preconditioner
+        CK(cudaMemsetAsync(pc.nchanged, 0, sizeof(int), h->stream));
+        RK(launch_count_changed(w.pi, pc.pi_built, S, pc.nchanged, h->stream));
+        CK(cudaMemcpyAsync(pc.h_nchanged, pc.nchanged, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+        CK(cudaStreamSynchronize(h->stream));
+        rebuild = (int64_t)*pc.h_nchanged * 1000 > S;
+        h->launches += 1;
+      }
+      if (rebuild) {
+        RK(launch_coarse_setup(h->d, w.pi, pck(h), pc.bw,
+                               PrecondScratch{pc.band, pc.cl, pc.cu, pc.dinv}, h->stream));
+        CK(cudaMemcpyAsync(pc.pi_built, w.pi, (size_t)S * 4, cudaMemcpyDeviceToDevice, h->stream));
+        pc.built = 1;
+        h->launches += 4;
+      }
     }
     if (host_loop) RK(inner_gmres(h, w.pi, 0, o.alpha, 0.0, o.restart, o.max_inner, nullptr, nullptr,
                                   w.phi, 0, 1));

@@ -570,6 +570,8 @@ int launch_coarse_setup(const DevMDP& d, const int32_t* pi, const PrecondK& p, i
                         const PrecondScratch& w, cudaStream_t st);
 // Per Arnoldi step (gated on STEP): Q_i and R Q_i, E_i, z = Q_i + Pr E_i.
 int launch_coarse_step(const PrecondK& p, int kt, cudaStream_t st);
+// *count += number of s in [0, S) with pi[s] != ref[s]
+int launch_count_changed(const int32_t* pi, const int32_t* ref, int64_t S, int* count, cudaStream_t st);
 // Gated on EST / RESTART / FINISH: ec = sum_{j <= i} y_j E_j.
 int launch_coarse_combine(const PrecondK& p, int kt, cudaStream_t st);
 

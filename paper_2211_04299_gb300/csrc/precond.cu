@@ -540,6 +540,17 @@ __global__ void coarse_combine_kernel(PrecondK p) {
   }
 }
 
+// Number of states whose action differs between two policies (block sums, one atomic per block).
+__global__ void count_changed_kernel(const int32_t* pi, const int32_t* ref, int64_t S, int* count) {
+  __shared__ int red[32];
+  int c = 0;
+  for (int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; s < S;
+       s += (int64_t)gridDim.x * blockDim.x)
+    c += pi[s] != ref[s];
+  c = block_sum(c, red);
+  if (threadIdx.x == 0 && c) atomicAdd(count, c);
+}
+
 inline int pc_grid(int64_t n, int per_block) {
   return (int)std::max<int64_t>(1, std::min<int64_t>((n + per_block - 1) / per_block,
                                                      (int64_t)num_sms() * 8));
@@ -617,6 +628,12 @@ int launch_coarse_step(const PrecondK& p, int kt, cudaStream_t st) {
     coarse_apply_kernel<double><<<gapply, PC_THREADS, 0, st>>>(p);
     coarse_prolong_kernel<double><<<pc_grid(p.S, 256), 256, 0, st>>>(p);
   }
+  return ok();
+}
+
+int launch_count_changed(const int32_t* pi, const int32_t* ref, int64_t S, int* count,
+                         cudaStream_t st) {
+  count_changed_kernel<<<pc_grid(S, 256), 256, 0, st>>>(pi, ref, S, count);
   return ok();
 }
 

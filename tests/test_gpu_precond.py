@@ -206,3 +206,23 @@ def test_device_coarse_inverse_matches_oracle(mg, gamma, block, narrow, vdt):
     rel = float(np.max(np.abs(inv.astype(np.float64) - exact)) / np.max(np.abs(exact)))
     assert rel <= 5e-6, rel
     assert float(np.min(inv)) >= -1e-6 * float(np.max(inv))
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp64"])
+def test_coarse_factor_reuse_gives_the_rebuilt_result(mg, prec):
+    """Reusing the coarse factors of an earlier policy (default: while at most 1 in 1000 states
+    changed action) and rebuilding them for every policy (MDP_FLAG_PC_REBUILD) both meet the
+    oracle's values; the preconditioner only changes the Krylov space."""
+    syn = banded(6000, prec, seed=1013)
+    m = oracle.from_synth(syn)
+    ref = oracle.policy_iteration(m, tol=1e-11)
+    h = mg.from_synth(syn)
+    tol = 1e-8 if prec == "mixed" else 1e-11
+    bound = 1e-6 if prec == "mixed" else 1e-10
+    for flags in (0, mg.MDP_FLAG_PC_REBUILD):
+        v, pi, st = mg.ipi_solve(h, mg.opts(tol=tol, precision=prec, precond_block=256,
+                                            flags=flags))
+        assert st["status"] == 0 and st["residual_inf"] <= tol, (flags, st)
+        assert rel_err(v, ref.v) <= bound
+        check_policy(pi, oracle.bellman(m, ref.v))
+    h.close()
