@@ -140,6 +140,16 @@ __device__ __forceinline__ void f2_acc(f2x& sh, f2x& sl, f2x p, f2x vh, f2x nvh,
   sh = s;
 }
 
+// The double-float value of a packed pair of running sums (hi pair sh, error pair sl): TwoSum of
+// the two high words, the two error words and its error added in FP32, then Fast2Sum.
+__device__ __forceinline__ dfl f2_to_df(f2x sh, f2x sl) {
+  float h0, h1, l0, l1;
+  f2_unpack(sh, h0, h1);
+  f2_unpack(sl, l0, l1);
+  const dfl t = two_sum(h0, h1);
+  return fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(l0, l1)));
+}
+
 // Running sum of products p * v with p FP32 and v double-float, accurate to about 2^-48
 // relative: each product is split exactly (TwoProduct), the high parts are added with
 // TwoSum and every error term goes to a low word; every 32 terms the chunk is folded into

@@ -605,10 +605,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
         if ((ch & 15) == 15) {
 #pragma unroll
           for (int g = 0; g < R; ++g) {
-            float h0, h1, l0, l1;
-            f2_unpack(sh[g], h0, h1);
-            f2_unpack(sl[g], l0, l1);
-            tot[g] = df_add(tot[g], df_add(two_sum(h0, l0), two_sum(h1, l1)));
+            tot[g] = df_add(tot[g], f2_to_df(sh[g], sl[g]));
             sh[g] = 0ull;
             sl[g] = 0ull;
           }
@@ -620,10 +617,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) sweep_dense_tma_kernel(SweepK p
 #pragma unroll
       for (int g = 0; g < TS_RMAX; ++g) {
         if (g < R) {
-          float h0, h1, l0, l1;
-          f2_unpack(sh[g], h0, h1);
-          f2_unpack(sl[g], l0, l1);
-          parts[g] = df_add(two_sum(h0, l0), two_sum(h1, l1));
+          parts[g] = f2_to_df(sh[g], sl[g]);
           if (folded) parts[g] = df_add(tot[g], parts[g]);
         } else {
           parts[g] = {0.f, 0.f};
