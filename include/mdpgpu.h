@@ -306,8 +306,12 @@ void mdp_batch_destroy(mdp_batch_t b);
 /* Stream for the batch's launches (a cudaStream_t; NULL = the batch's own stream). */
 int mdp_batch_set_stream(mdp_batch_t b, void* stream);
 /* Autotuner: for each ELL row length present, times the batched Bellman sweep and the
- * batched matvec with 1, 2, 4 and 8 lanes per row and keeps the fastest (this changes only
- * the order of floating-point additions).  Runs kernels on the batch's stream; synchronous. */
+ * batched matvec with 1, 2, 4 and 8 lanes per row (warp shape) and keeps the fastest, then, with
+ * that shape, times row tiles of 1/2, 1, 2 and 4 times the library's states per virtual block
+ * (about 512 KB of P per sweep block and 256 KB per matvec block) and keeps the fastest; tiles
+ * whose matvec partial sums would not fit the instance's workspace are skipped.  Both change
+ * only the order of floating-point additions (mdp_batch_geometry reports the choice, so a single
+ * solve can reproduce an instance bit for bit).  Runs kernels on the batch's stream; synchronous. */
 int mdp_batch_tune(mdp_batch_t b);
 /* Kernel shape of instance i (any output may be NULL). */
 int mdp_batch_geometry(mdp_batch_t b, int32_t i, int32_t* lanes_sweep, int32_t* lanes_matvec,

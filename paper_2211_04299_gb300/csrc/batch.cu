@@ -699,6 +699,13 @@ int upload_list(mdp_batch_s* b, const BatchList& L, const std::vector<int>& ids,
   return MDP_OK;
 }
 
+}  // namespace
+namespace mdp {
+static size_t partial_bytes(const BatchInst& I);
+static void batch_geometry(const DevMDP& d, BatchInst& I);
+}  // namespace mdp
+namespace {
+
 int tune_batch(mdp_batch_s* b) {
   // group instances by padded ELL row length
   std::vector<int> kps;
@@ -737,10 +744,62 @@ int tune_batch(mdp_batch_s* b) {
           best_c = c;
         }
       }
-      const int empty = 0;
-      BCK(cudaMemcpy(L.count, &empty, sizeof(int), cudaMemcpyHostToDevice));
       for (int j : ids) (fam == 0 ? saved[j].cls_sw : saved[j].cls_mv) = best_c;
       for (int j : ids) (fam == 0 ? b->table[j].cls_sw : b->table[j].cls_mv) = best_c;
+      // row tiles of the chosen lane class: the library's states per virtual block scaled by
+      // 1, 1/2, 2 and 4 (block counts scaled inversely); a candidate whose matvec partial sums
+      // would not fit the instance's workspace is skipped
+      std::vector<int> base(ids.size());
+      for (size_t i = 0; i < ids.size(); ++i)
+        base[i] = fam == 0 ? b->table[ids[i]].nb_sw : b->table[ids[i]].nb_mv;
+      const double scales[4] = {1.0, 0.5, 2.0, 4.0};
+      float best_t = 1e30f;
+      int best_s = 0;
+      for (int si = 0; si < 4; ++si) {
+        bool fits = true;
+        int64_t tot_s = 0;
+        for (size_t i = 0; i < ids.size(); ++i) {
+          BatchInst& I = b->table[ids[i]];
+          const int nb = (int)std::max<int64_t>(
+              1, std::min<int64_t>(MAX_RED_BLOCKS, (int64_t)std::ceil(base[i] / scales[si])));
+          if (fam == 0) {
+            I.nb_sw = nb;
+          } else {
+            BatchInst t = I, t0 = I;  // t0: the create-time geometry the workspace was sized for
+            batch_geometry(t0.d, t0);
+            t.nb_mv = nb;
+            if (partial_bytes(t) > partial_bytes(t0)) fits = false;
+            I.nb_mv = nb;
+          }
+          tot_s += nb;
+        }
+        if (!fits) continue;
+        BRK(upload_table(b));
+        BRK(upload_list(b, L, ids, fam == 0));
+        const int g2 = (int)std::min<int64_t>(fam == 0 ? batch_sweep_grid() : batch_matvec_grid(), tot_s);
+        int r = MDP_OK;
+        const float ms = time_best(b, [&]() {
+          if (r != MDP_OK) return;
+          r = fam == 0 ? launch_batch_sweep(b->B, g2, b->stream)
+                       : launch_batch_matvec(b->B, 2, g2, b->stream);
+        });
+        BRK(r);
+        BCK(cudaGetLastError());
+        if (ms < best_t) {
+          best_t = ms;
+          best_s = si;
+        }
+      }
+      for (size_t i = 0; i < ids.size(); ++i) {
+        const int nb = (int)std::max<int64_t>(
+            1, std::min<int64_t>(MAX_RED_BLOCKS, (int64_t)std::ceil(base[i] / scales[best_s])));
+        BatchInst& I = b->table[ids[i]];
+        BatchInst& Sv = saved[ids[i]];
+        if (fam == 0) I.nb_sw = Sv.nb_sw = nb;
+        else I.nb_mv = Sv.nb_mv = nb;
+      }
+      const int empty = 0;
+      BCK(cudaMemcpy(L.count, &empty, sizeof(int), cudaMemcpyHostToDevice));
     }
   }
   b->table = saved;
