@@ -196,12 +196,7 @@ struct mdp_shard_s {
 
 namespace {
 
-thread_local std::string g_shard_err;
-
-int sfail(int code, const char* msg) {
-  g_shard_err = msg;
-  return set_error(code, msg);
-}
+int sfail(int code, const char* msg) { return set_error(code, msg); }
 
 void shard_free_ws(mdp_shard_t h) {
   void* dev[] = {h->vglob, h->xglob, h->v, h->tv, h->phi, h->w, h->x0, h->r, h->cand, h->Q,
@@ -467,7 +462,7 @@ int shard_ipi(mdp_shard_t h, const mdp_comm* comm, const mdp_opts& o, double* v_
   st.status = status;
   st.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (st_user) *st_user = st;
-  if (status != MDP_OK) g_shard_err = "iteration cap reached";
+  if (status != MDP_OK) set_error(status, "iteration cap reached before ||T(v)-v||_inf <= tol");
   return status;
 }
 
@@ -544,7 +539,6 @@ void mdp_shard_destroy(mdp_shard_t h) {
 
 int ipi_solve_sharded(mdp_shard_t h, const mdp_comm* comm, const mdp_opts* opts, double* v_out,
                       int32_t* pi_out, mdp_stats* stats) {
-  g_shard_err.clear();
   if (!h || !comm || !v_out || !comm->allgather || !comm->allreduce || !comm->row_begin)
     return sfail(MDP_EINVAL, "null shard, communicator, callback or output");
   if (comm->world < 1 || comm->rank < 0 || comm->rank >= comm->world ||

@@ -103,3 +103,56 @@ def test_sharded_solve_matches_oracle(world, kind, vdt):
     assert np.array_equal(pi[sure], sw.pi[sure])
     # the contraction bound certifies every state of the gathered v
     assert oracle.bellman(m, v).res_inf <= g * tol + 1e-12 * np.max(np.abs(v))
+
+
+def _mismatch_main(port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK="0", WORLD_SIZE="1")
+    sys.path.insert(0, ROOT)
+    try:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(0)
+        import paper_2211_04299_gb300 as mg
+        dist.init_process_group("gloo", rank=0, world_size=1)
+        syn = _make("uniform", np.float64)
+        h = mg.mdp_shard_create(syn.S, 0, syn.col, syn.val, syn.g, syn.gamma)
+        codes = []
+        for rb in ([0, syn.S - 1], [0, syn.S + 1]):   # partitions that do not match the shard
+            try:
+                mg.ipi_solve_sharded(h, mg.ShardComm(np.array(rb)), mg.opts())
+                codes.append(0)
+            except mg.MDPError as e:
+                codes.append(e.code)
+        v, pi, st = mg.ipi_solve_sharded(h, mg.ShardComm(mg.row_partition(syn.S, 1)),
+                                         mg.opts(tol=1e-10, precision="fp64"))
+        bad_col = syn.col.copy()
+        bad_col[0, 5, 0] = syn.S
+        try:
+            mg.mdp_shard_create(syn.S, 0, bad_col, syn.val, syn.g, syn.gamma)
+            codes.append(0)
+        except mg.MDPError as e:
+            codes.append(e.code)
+        h.close()
+        dist.destroy_process_group()
+        q.put((codes, v, st, None))
+    except Exception as e:
+        q.put((None, None, None, repr(e)))
+
+
+def test_sharded_solve_rejects_a_mismatched_partition_and_runs_on_one_rank():
+    """A communicator whose row partition does not match the shard is rejected (MDP_EINVAL)
+    before any exchange, as is a column index outside [0, S); one rank owning every row solves
+    to the oracle's values."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    p = ctx.Process(target=_mismatch_main, args=(_free_port(), q))
+    p.start()
+    codes, v, st, err = q.get(timeout=600)
+    p.join(timeout=120)
+    assert err is None, err
+    assert codes == [-1, -1, -1]
+    syn = _make("uniform", np.float64)
+    ref = oracle.gmres_policy_iteration(oracle.from_synth(syn), alpha=0.1, W=30, tol=1e-13)
+    assert st["status"] == 0
+    assert float(np.max(np.abs(v - ref.v)) / np.max(np.abs(ref.v))) <= 1e-10
