@@ -504,3 +504,26 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable(mg):
     assert rel_err(Tv, sw.Tv) <= 1e-12
     check_policy(pi, sw)
     h.close()
+
+
+def test_allocation_failure_reports_enomem_and_the_device_stays_usable(mg):
+    """An MDP far larger than the device (2^31 - 65 states, 16 actions, 32 entries a row: about
+    4.4 TB of values) fails in its first device allocation with MDP_ENOMEM, before any input is
+    read (the inputs here are small placeholder buffers), and the next handle works."""
+    import ctypes
+    import torch
+    lib = mg.lib()
+    dummy = torch.zeros(64, dtype=torch.float64, device="cuda")
+    p = ctypes.c_void_p(dummy.data_ptr())
+    h = ctypes.c_void_p()
+    S = (1 << 31) - 65
+    rc = lib.mdp_create_ell_dev(S, 16, 32, p, p, mg.MDP_F32, p, 0.9, None, ctypes.byref(h))
+    assert rc == -2 and not h.value                         # MDP_ENOMEM, no handle
+    assert b"cudaMalloc" in lib.mdp_last_error()
+    syn = make("ell", 300, 4, 7, seed=2, val_dtype=np.float32)
+    hh = mg.from_synth(syn)
+    v = np.random.default_rng(1).normal(size=300)
+    sw = oracle.bellman(oracle.from_synth(syn), v)
+    Tv, pi, res = mg.bellman_apply(hh, v, precision="mixed")
+    assert rel_err(Tv, sw.Tv) <= 1e-12
+    hh.close()
