@@ -239,10 +239,21 @@ KrylovBufs kbufs(mdp_t h) {
 constexpr int64_t PC_NC_MAX = 8192;  // coarse blocks (J_c^{-1} is nc^2 FP32 values)
 
 // Coarse half-bandwidth of the transition data for blocks of 2^lb states (cached until the
-// data is reloaded).
+// data is reloaded).  When the upload's validation measured the column reach r = max |col - s|,
+// the bound |block(col) - block(s)| <= (r + b - 1) / b (b = 2^lb) is used without a pass over
+// the columns: a band a block wider than the data needs only holds zeros, which the GTH
+// elimination and the inverse carry through unchanged.
 int coarse_bandwidth(mdp_t h, int lb, int* bw) {
   auto& p = h->pc;
   if (p.bw_lb == lb) {
+    *bw = p.bw_cached;
+    return MDP_OK;
+  }
+  if (h->d.span >= 0) {
+    const int64_t b = (int64_t)1 << lb;
+    const int64_t hb = (h->d.span + b - 1) >> lb;
+    p.bw_lb = lb;
+    p.bw_cached = (int)std::min<int64_t>(hb, INT32_MAX);
     *bw = p.bw_cached;
     return MDP_OK;
   }
