@@ -762,16 +762,81 @@ __device__ __forceinline__ void cgs_dots_body(const KB& b, GridPos gp) {
   block_reduce_cols<KT, MAXM>(acc, m, (KT*)b.partials, gp);
   if (!arrive_last(b.counter, gp.nb)) return;
   reduce_dots<KT>((const KT*)b.partials, m, c->c1, c->c1f, gp);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // w - Q c1 keeps ||w||^2 - ||c1||^2 of w's squared norm (Q orthonormal); when that is more
+    // than half, the projection cancelled little and one pass is enough (the criterion of
+    // Daniel, Gragg, Kaufman and Stewart with eta = 1/sqrt(2)); otherwise the second projection
+    // runs (CGS2).  ||w|| = ||J q_i||_2 was measured by the matvec.
+    double h2 = 0.0;
+    for (int j = 0; j < m; ++j) h2 += c->c1[j] * c->c1[j];
+    c->once = h2 < 0.5 * c->last_nrm2 * c->last_nrm2 ? 1 : 0;
+  }
+}
+
+__device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis);
+
+// w -= Q coef, then ||w||_2 and the Givens update (the last projection of a step).  With
+// zero_c2 (a step with one projection) the second coefficients are set to zero, since column i
+// of H is c1 + c2.
+template <class KT, int MAXM, bool KEEP>
+__device__ __forceinline__ void cgs_update_norm(const KB& b, GridPos gp, const double* coefd,
+                                                const float* coeff, bool zero_c2) {
+  const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
+  using T = TSv<KT>;
+  GmresCtl* c = b.ctl;
+  const int i = c->i, m = i + 1;
+  KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
+  const KT* Q = (const KT*)b.Q;
+  __shared__ KT cf[WMAX + 1];
+  stage_coefs<KT>(cf, coefd, coeff, m);
+  int64_t u0, u1;
+  block_units<KT>(b.S, u0, u1, gp);
+  KT ss = 0;
+  for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
+    typename T::V wv = tsld<KT, KEEP>(pol, w + u * T::R);
+#pragma unroll
+    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
+      if (j0 < m) {
+        typename T::V q[TS_BATCH];
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t)
+          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
+#pragma unroll
+        for (int t = 0; t < TS_BATCH; ++t) wv = T::axpy(-cf[j0 + t], q[t], wv);
+      }
+    }
+    T::st(w + u * T::R, wv);
+    ss += T::dot(wv, wv);
+  }
+  __shared__ KT shr[32];
+  KT bs = block_sum(ss, shr);
+  KT* part = (KT*)b.partials;
+  if (threadIdx.x == 0) part[gp.bid] = bs;
+  if (!arrive_last(b.counter, gp.nb)) return;
+  KT t = 0;
+  for (int bb = threadIdx.x; bb < gp.nb; bb += blockDim.x) t += __ldcg(part + bb);
+  t = block_sum(t, shr);
+  if (threadIdx.x == 0) {
+    if (zero_c2)
+      for (int j = 0; j < m; ++j) c->c2[j] = 0.0;
+    givens_and_decide(c, sqrt((double)t), sizeof(KT) == 4);
+  }
 }
 
 // CGS2 pass 1 update and pass 2 projection: w -= Q c1, then c2 = Q^T w.  The second read of
-// each Q_j unit follows the first within the same thread and is served by L1.
+// each Q_j unit follows the first within the same thread and is served by L1.  When the first
+// pass found one projection enough, this pass is the last one instead.
 template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void cgs_axpy_dots_body(const KB& b, GridPos gp) {
   const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
   using T = TSv<KT>;
   GmresCtl* c = b.ctl;
   if (*(volatile int*)&c->mode != GM_STEP) return;
+  if (c->once) {
+    cgs_update_norm<KT, MAXM, KEEP>(b, gp, c->c1, c->c1f, true);
+    return;
+  }
   const int i = c->i, m = i + 1;
   KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
   const KT* Q = (const KT*)b.Q;
@@ -893,43 +958,9 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
 // CGS2 pass 2 update, ||w||_2 and the Givens step: w -= Q c2.
 template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void cgs_axpy_norm_body(const KB& b, GridPos gp) {
-  const uint64_t pol = KEEP ? l2_keep_policy() : 0ull;
-  using T = TSv<KT>;
   GmresCtl* c = b.ctl;
-  if (*(volatile int*)&c->mode != GM_STEP) return;
-  const int i = c->i, m = i + 1;
-  KT* w = (KT*)((i & 1) ? b.w1 : b.w0);
-  const KT* Q = (const KT*)b.Q;
-  __shared__ KT cf[WMAX + 1];
-  stage_coefs<KT>(cf, c->c2, c->c2f, m);
-  int64_t u0, u1;
-  block_units<KT>(b.S, u0, u1, gp);
-  KT ss = 0;
-  for (int64_t u = u0 + threadIdx.x; u < u1; u += blockDim.x) {
-    typename T::V wv = tsld<KT, KEEP>(pol, w + u * T::R);
-#pragma unroll
-    for (int j0 = 0; j0 < MAXM; j0 += TS_BATCH) {
-      if (j0 < m) {
-        typename T::V q[TS_BATCH];
-#pragma unroll
-        for (int t = 0; t < TS_BATCH; ++t)
-          q[t] = tsld<KT, KEEP>(pol, Q + (int64_t)min(j0 + t, m - 1) * b.ldq + u * T::R);
-#pragma unroll
-        for (int t = 0; t < TS_BATCH; ++t) wv = T::axpy(-cf[j0 + t], q[t], wv);
-      }
-    }
-    T::st(w + u * T::R, wv);
-    ss += T::dot(wv, wv);
-  }
-  __shared__ KT shr[32];
-  KT bs = block_sum(ss, shr);
-  KT* part = (KT*)b.partials;
-  if (threadIdx.x == 0) part[gp.bid] = bs;
-  if (!arrive_last(b.counter, gp.nb)) return;
-  KT t = 0;
-  for (int bb = threadIdx.x; bb < gp.nb; bb += blockDim.x) t += __ldcg(part + bb);
-  t = block_sum(t, shr);
-  if (threadIdx.x == 0) givens_and_decide(c, sqrt((double)t), sizeof(KT) == 4);
+  if (*(volatile int*)&c->mode != GM_STEP || c->once) return;  // once: pass 2 finished the step
+  cgs_update_norm<KT, MAXM, KEEP>(b, gp, c->c2, c->c2f, false);
 }
 
 // x + e on the rows of a vector unit that lie below S (the block of 2^lb >= 4 states is the

@@ -385,6 +385,7 @@ struct GmresCtl {
   double c1[WMAX + 1], c2[WMAX + 1];  // CGS2 coefficients of pass 1 and pass 2
   float c1f[WMAX + 1], c2f[WMAX + 1], yf[WMAX], zf[WMAX + 1];
   float xscalef;
+  int once;         // this step needs no second projection (set by the first pass)
 };
 
 // Right-hand side of the inexact stopping rule for outer residual res = ||Phi_k||_inf
