@@ -1,7 +1,8 @@
 // Restarted GMRES(W) for the inexact policy evaluation of Alg. 2 (paper Sec. 2.2, 3.1):
 //
 //   P^pi matvec   w = J^pi q = q - gamma P^pi q, rows of P_{pi(s)} gathered on the fly
-//   Arnoldi       classical Gram-Schmidt with one re-orthogonalisation (CGS2), the Hessenberg
+//   Arnoldi       classical Gram-Schmidt, re-orthogonalised once (CGS2) when the first projection
+//                 cancelled more than half of the norm, the Hessenberg
 //                 column H[0..i+1][i] in FP64
 //   least squares Givens rotations on H in FP64, |gv[i+1]| = ||beta e1 - H y||_2
 //   stopping rule ||g^pi - J^pi V||_inf <= thr, tested on the true residual; a cheap bound
@@ -955,7 +956,7 @@ __device__ void givens_and_decide(GmresCtl* c, double hnext, bool fp32_basis) {
   c->mode = mode;
 }
 
-// CGS2 pass 2 update, ||w||_2 and the Givens step: w -= Q c2.
+// CGS2 pass 2 update, ||w||_2 and the Givens step: w -= Q c2 (idle when pass 2 finished the step).
 template <class KT, int MAXM, bool KEEP = false>
 __device__ __forceinline__ void cgs_axpy_norm_body(const KB& b, GridPos gp) {
   GmresCtl* c = b.ctl;

@@ -530,7 +530,8 @@ struct KrylovBufs {
   int lb = 0;                // to each state of its block (block = 2^lb states)
 };
 
-// One Arnoldi step after the matvec: CGS2 (two passes) + norm + Givens + mode decision.
+// One Arnoldi step after the matvec: Gram-Schmidt (one or two projections) + norm + Givens +
+// mode decision.
 int launch_cgs2_givens(const KrylovBufs& B, cudaStream_t st);
 // Gated on EST/RESTART/FINISH: candidate = delta_base + Q_{0..i} y and, in EST mode, the
 // Arnoldi-relation bound ||Q_{0..i} z + z_{i+1} w / hnext||_inf that decides CHECK or not.
