@@ -240,7 +240,7 @@ __device__ __forceinline__ void mv_cp_async(KT* smem, const KT* gmem) {
 }
 
 template <class PT, class KT, int T>
-__global__ void __launch_bounds__(256) matvec_ell_window_kernel(MatvecK p, int64_t steps_per_block) {
+__global__ void __launch_bounds__(256) matvec_ell_window_kernel(MatvecK p) {
   __shared__ KT ring[MV_RING];
   const MvIO<KT> io = resolve<KT>(p);
   if (!io.run) return;  // uniform over the grid
@@ -252,26 +252,26 @@ __global__ void __launch_bounds__(256) matvec_ell_window_kernel(MatvecK p, int64
   const KT* u = (const KT*)p.u;
   const KT ca = (KT)p.a, cb = (KT)p.b, cc = (KT)p.c;
   const int64_t span = d.span;
-  const int64_t nsteps = (d.S + MV_NB - 1) / MV_NB;
-  const int64_t st0 = (int64_t)blockIdx.x * steps_per_block;
-  const int64_t st1 = min(nsteps, st0 + steps_per_block);
+  // this block's states: an equal share of the 32-state units, walked in steps of MV_NB
+  const int64_t nu = (d.S + 31) >> 5;
+  const int64_t sb = 32 * (nu * blockIdx.x / gridDim.x);
+  const int64_t se = min(d.S, 32 * (nu * (blockIdx.x + 1) / gridDim.x));
   auto fill = [&](int64_t x0, int64_t x1) {
     const int64_t a0 = max(x0, (int64_t)0), a1 = min(x1, d.S);
     for (int64_t x = a0 + threadIdx.x; x < a1; x += blockDim.x) mv_cp_async(ring + (x & (MV_RING - 1)), io.x + x);
     asm volatile("cp.async.commit_group;" ::: "memory");
   };
   KT mx = 0, ss = 0;
-  if (st0 < st1) {
-    const int64_t lo = st0 * MV_NB;
-    fill(lo - span, lo + MV_NB + span);
+  if (sb < se) {
+    fill(sb - span, min(sb + MV_NB, se) + span);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    for (int64_t stp = st0; stp < st1; ++stp) {
-      const int64_t s_lo = stp * MV_NB, s_hi = s_lo + MV_NB;
-      if (stp + 1 < st1) fill(s_hi + span, s_hi + MV_NB + span);
-      for (int64_t sb = s_lo; sb < s_hi; sb += nteams) {
-        const int64_t s = sb + team;
-        const bool act = s < d.S;
+    for (int64_t s_lo = sb; s_lo < se; s_lo += MV_NB) {
+      const int64_t s_hi = min(s_lo + MV_NB, se);
+      if (s_hi < se) fill(s_hi + span, min(s_hi + MV_NB, se) + span);
+      for (int64_t s1 = s_lo; s1 < s_hi; s1 += nteams) {
+        const int64_t s = s1 + team;
+        const bool act = s < s_hi;
         KT acc = 0;
         if (act) {
           const int64_t base = ((int64_t)s * d.A + p.pi[s]) * d.kp;
@@ -576,16 +576,15 @@ int launch_mv_typed(const MatvecLaunch& L, cudaStream_t st) {
       // the windowed kernel wants two vectors per lane in flight (measured: banded S = 10^6,
       // 4 lanes per row 153 us per Arnoldi step against 180 us with 8)
       const int Tw = L.lanes > 0 ? L.lanes : std::max(1, T / 2);
-      // banded columns: shared-memory window of x (block-contiguous steps of MV_NB states)
-      const int64_t nsteps = (d.S + MV_NB - 1) / MV_NB;
-      int64_t blocks = std::min<int64_t>(std::min<int64_t>((int64_t)num_sms() * 4, nsteps), MAX_RED_BLOCKS);
-      const int64_t spb = (nsteps + blocks - 1) / blocks;
-      const int grid = (int)((nsteps + spb - 1) / spb);
+      // banded columns: shared-memory window of x (each block a contiguous range of states,
+      // at least one step of MV_NB)
+      const int grid = (int)std::max<int64_t>(
+          1, std::min<int64_t>(std::min<int64_t>((int64_t)num_sms() * 4, d.S / MV_NB), MAX_RED_BLOCKS));
       switch (Tw) {
-        case 1: matvec_ell_window_kernel<PT, KT, 1><<<grid, 256, 0, st>>>(p, spb); break;
-        case 2: matvec_ell_window_kernel<PT, KT, 2><<<grid, 256, 0, st>>>(p, spb); break;
-        case 4: matvec_ell_window_kernel<PT, KT, 4><<<grid, 256, 0, st>>>(p, spb); break;
-        case 8: matvec_ell_window_kernel<PT, KT, 8><<<grid, 256, 0, st>>>(p, spb); break;
+        case 1: matvec_ell_window_kernel<PT, KT, 1><<<grid, 256, 0, st>>>(p); break;
+        case 2: matvec_ell_window_kernel<PT, KT, 2><<<grid, 256, 0, st>>>(p); break;
+        case 4: matvec_ell_window_kernel<PT, KT, 4><<<grid, 256, 0, st>>>(p); break;
+        case 8: matvec_ell_window_kernel<PT, KT, 8><<<grid, 256, 0, st>>>(p); break;
         default: return MDP_EINVAL;
       }
       return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;

@@ -39,6 +39,10 @@ struct ArF64 {
   static __device__ __forceinline__ Qt qval(const DevMDP& d, int64_t s, int a, Qt sum) {
     return fma(d.gamma, sum, d.g64[s * d.A + a]);
   }
+  // the cost, loaded before a row's sum (so its latency overlaps the row) and applied after
+  using G = double;
+  static __device__ __forceinline__ G gload(const DevMDP& d, int64_t s, int a) { return __ldg(d.g64 + s * d.A + a); }
+  static __device__ __forceinline__ Qt qval_g(const DevMDP& d, G g, Qt sum) { return fma(d.gamma, sum, g); }
   static __device__ __forceinline__ Qt inf() { return __longlong_as_double(0x7ff0000000000000LL); }
   static __device__ __forceinline__ bool lt(Qt a, Qt b) { return a < b; }
   static __device__ __forceinline__ Qt sub(Qt a, V b) { return a - b; }
@@ -78,6 +82,11 @@ struct ArDF {
   }
   static __device__ __forceinline__ Qt qval(const DevMDP& d, int64_t s, int a, Qt sum) {
     float2 g = __ldg(d.gdf + s * d.A + a);
+    return df_add({g.x, g.y}, df_mul(dfl{d.gamma_hi, d.gamma_lo}, sum));
+  }
+  using G = float2;
+  static __device__ __forceinline__ G gload(const DevMDP& d, int64_t s, int a) { return __ldg(d.gdf + s * d.A + a); }
+  static __device__ __forceinline__ Qt qval_g(const DevMDP& d, G g, Qt sum) {
     return df_add({g.x, g.y}, df_mul(dfl{d.gamma_hi, d.gamma_lo}, sum));
   }
   static __device__ __forceinline__ Qt inf() { return {__int_as_float(0x7f800000), 0.f}; }
@@ -771,7 +780,11 @@ __device__ __forceinline__ Pick<AR> ell_state_group(const SweepK& p, const EllLa
     const int a = act ? (p.pi_in ? p.pi_in[s] : a_local) : 0;
     typename AR::Acc acc;
     acc.init();
+    typename AR::G gq{};  // windowed sweep: the cost is loaded before the row's sum, so its
+                          // latency overlaps the row (the L1-bound global-gather sweeps load it
+                          // after the sum, which measured faster there)
     if (act) {
+      if constexpr (Gather::kWindow) gq = AR::gload(d, s, a);
       const int64_t base = ((int64_t)s * d.A + a) * d.kp;
       for (int q0 = L.tl; q0 < L.nvec; q0 += 2 * T) {
         Vec4<PT> pv[2];
@@ -810,7 +823,11 @@ __device__ __forceinline__ Pick<AR> ell_state_group(const SweepK& p, const EllLa
       }
     }
     const Qt sum = AR::reduce_team(acc.result(), T);
-    const Qt q = act ? AR::qval(d, s, a, sum) : AR::inf();
+    Qt q = AR::inf();
+    if (act) {
+      if constexpr (Gather::kWindow) q = AR::qval_g(d, gq, sum);
+      else q = AR::qval(d, s, a, sum);
+    }
     const bool allowed = act && (p.pi_in ? true : (d.mask ? d.mask[s * d.A + a] != 0 : true));
     // reference-policy row of this pass (when it lies here): its lane holds qref.  Every
     // lane takes part in the shuffle; only lanes whose reference row is in this pass keep it.
@@ -921,7 +938,7 @@ __device__ __forceinline__ void win_cp8(void* smem, const void* gmem) {
 }
 
 template <class PT, class AR, int T>
-__global__ void __launch_bounds__(256, 4) sweep_ell_window_kernel(SweepK p, int64_t steps_per_block) {
+__global__ void __launch_bounds__(256, 4) sweep_ell_window_kernel(SweepK p) {
   using V = typename AR::V;
   static_assert(sizeof(V) == 8, "window entries are 8 bytes");
   __shared__ V ring[WIN_RING];
@@ -929,9 +946,11 @@ __global__ void __launch_bounds__(256, 4) sweep_ell_window_kernel(SweepK p, int6
   const EllLanes L = ell_lanes<T>(p);
   const int warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   const int64_t span = d.span;
-  const int64_t nsteps = (d.S + WIN_NB - 1) / WIN_NB;
-  const int64_t st0 = (int64_t)blockIdx.x * steps_per_block;
-  const int64_t st1 = min(nsteps, st0 + steps_per_block);
+  // this block's states: an equal share of the 32-state units (so every SM, holding the same
+  // number of blocks, gets the same work), walked in steps of WIN_NB
+  const int64_t nu = (d.S + 31) >> 5;
+  const int64_t sb = 32 * (nu * blockIdx.x / gridDim.x);
+  const int64_t se = min(d.S, 32 * (nu * (blockIdx.x + 1) / gridDim.x));
   const V* v = (const V*)p.v;
   auto fill = [&](int64_t x0, int64_t x1) {  // v[x], x in [x0, x1) and in [0, S), one group
     const int64_t a0 = max(x0, (int64_t)0), a1 = min(x1, d.S);
@@ -943,17 +962,16 @@ __global__ void __launch_bounds__(256, 4) sweep_ell_window_kernel(SweepK p, int6
   nm.init();
   EmitQueue<AR> eq;
   eq.init();
-  if (st0 < st1) {
-    const int64_t lo = st0 * WIN_NB;
-    fill(lo - span, lo + WIN_NB + span);
+  if (sb < se) {
+    fill(sb - span, min(sb + WIN_NB, se) + span);
     asm volatile("cp.async.wait_group 0;" ::: "memory");
     __syncthreads();
-    for (int64_t stp = st0; stp < st1; ++stp) {
-      const int64_t s_lo = stp * WIN_NB, s_hi = s_lo + WIN_NB;
+    for (int64_t s_lo = sb; s_lo < se; s_lo += WIN_NB) {
+      const int64_t s_hi = min(s_lo + WIN_NB, se);
       // the next step's new entries go where entries below s_lo - span were (the ring holds
       // 2 WIN_NB + 2 span entries, so they never overwrite this step's window)
-      if (stp + 1 < st1) fill(s_hi + span, s_hi + WIN_NB + span);
-      for (int64_t s0 = s_lo + warp * L.G; s0 < s_hi && s0 < d.S; s0 += nwarp * L.G)
+      if (s_hi < se) fill(s_hi + span, min(s_hi + WIN_NB, se) + span);
+      for (int64_t s0 = s_lo + warp * L.G; s0 < s_hi; s0 += nwarp * L.G)
         eq.push(p, L, s0, ell_state_group<PT, AR, T>(p, L, s0, gather), nm);
       asm volatile("cp.async.wait_group 0;" ::: "memory");
       __syncthreads();
@@ -1054,18 +1072,16 @@ int launch_typed(const SweepLaunch& L, cudaStream_t st) {
   } else {
     const int T = L.lanes > 0 ? L.lanes : ell_sweep_lanes_default(d);
     if (d.span >= 0 && d.span <= WIN_SPAN_MAX && !L.no_window && d.S >= 4 * WIN_NB) {
-      // banded columns: shared-memory window of v (block-contiguous steps of WIN_NB states)
-      const int64_t nsteps = (d.S + WIN_NB - 1) / WIN_NB;
+      // banded columns: shared-memory window of v (each block a contiguous range of states,
+      // at least one step of WIN_NB)
       int64_t blocks = L.grid > 0 ? L.grid : (int64_t)num_sms() * 4;
-      blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, nsteps));
-      blocks = std::min<int64_t>(blocks, MAX_RED_BLOCKS);
-      const int64_t spb = (nsteps + blocks - 1) / blocks;
-      const int grid = (int)((nsteps + spb - 1) / spb);
+      blocks = std::max<int64_t>(1, std::min<int64_t>(blocks, d.S / WIN_NB));
+      const int grid = (int)std::min<int64_t>(blocks, MAX_RED_BLOCKS);
       switch (T) {
-        case 1: sweep_ell_window_kernel<PT, AR, 1><<<grid, 256, 0, st>>>(p, spb); break;
-        case 2: sweep_ell_window_kernel<PT, AR, 2><<<grid, 256, 0, st>>>(p, spb); break;
-        case 4: sweep_ell_window_kernel<PT, AR, 4><<<grid, 256, 0, st>>>(p, spb); break;
-        case 8: sweep_ell_window_kernel<PT, AR, 8><<<grid, 256, 0, st>>>(p, spb); break;
+        case 1: sweep_ell_window_kernel<PT, AR, 1><<<grid, 256, 0, st>>>(p); break;
+        case 2: sweep_ell_window_kernel<PT, AR, 2><<<grid, 256, 0, st>>>(p); break;
+        case 4: sweep_ell_window_kernel<PT, AR, 4><<<grid, 256, 0, st>>>(p); break;
+        case 8: sweep_ell_window_kernel<PT, AR, 8><<<grid, 256, 0, st>>>(p); break;
         default: return MDP_EINVAL;
       }
       return cudaGetLastError() == cudaSuccess ? MDP_OK : MDP_EDEVICE;
