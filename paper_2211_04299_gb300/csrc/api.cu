@@ -978,6 +978,7 @@ int enqueue_upload(mdp_t h, const void* P, const int32_t* col, const double* g,
   int* flags = h->vflags;  // allocated with the handle (a per-load cudaFree would stall the device)
   CK(cudaMemsetAsync(flags, 0, 8 * sizeof(int), s));
   RK(launch_validate(d, flags, s));
+  RK(launch_ell_bank_order(d, h->P, h->col, flags, s));
   CK(cudaMemcpyAsync(h->h_vflags, flags, 8 * sizeof(int), cudaMemcpyDeviceToHost, s));
   h->vpending = 1;
   return MDP_OK;

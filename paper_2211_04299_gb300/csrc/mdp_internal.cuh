@@ -600,6 +600,12 @@ int launch_cost_transpose(const double* gAS, double* gSA, float2* gdf, int64_t S
 // Device-side validation of uploaded data: error flags into flags[0..4] (values, columns, row
 // sums, costs, allowed actions) and, for ELL, the largest |col - s| into flags[6] (atomicMax).
 int launch_validate(const DevMDP& d, int* flags, cudaStream_t st);
+// After launch_validate on the same stream: reorder the nonzeros within each row of banded ELL
+// data (validation's flags clean, column reach within the windowed sweep's) so that the
+// windowed sweep's shared-memory gathers spread over the banks (sweep.cu).  val and col are
+// the handle's own copies of d.P and d.col.
+int launch_ell_bank_order(const DevMDP& d, void* val, int32_t* col, const int* flags,
+                          cudaStream_t st);
 // flags[5] |= 1 when a policy entry is out of range or disallowed by the mask.
 int launch_check_policy(const int32_t* pi, int64_t S, int32_t A, const uint8_t* mask, int* flags,
                         cudaStream_t st);
