@@ -207,6 +207,7 @@ int start_upload(mdp_server_s* s, Req* r) {
   SRK(launch_cost_transpose(gst, g64, gdf, d.S, d.A, s->us));
   SCK(cudaMemsetAsync(r->flags, 0, FLAG_INTS * sizeof(int), s->us));
   SRK(launch_validate(d, r->flags, s->us));
+  SRK(launch_ell_bank_order(d, val, col, r->flags, s->us));  // the handles' order, bit for bit
   SCK(cudaMemcpyAsync(s->h_flags + (size_t)r->slot * FLAG_INTS, r->flags, FLAG_INTS * sizeof(int),
                       cudaMemcpyDeviceToHost, s->us));
   r->ev = get_event(s);

@@ -989,23 +989,28 @@ __global__ void __launch_bounds__(256, 4) sweep_ell_window_kernel(SweepK p) {
 // (it changes only the order of the row's sum, and every kernel reads the same stored order),
 // so after validation, banded data is reordered for the sweep's lane layout (ell_lanes with the
 // default lane count): the rows whose lanes form one half-warp are visited in lane order, and
-// each nonzero of a row, in stored order, moves to the free slot of its row whose gather
-// instruction has so far the fewest entries in the nonzero's bank pair (ties: the lowest slot).
-// On config-3 columns this greedy placement takes the expected wavefronts of a gather from
-// 6.1 to 3.9 (a full assignment per row, by the Hungarian method, reaches 4.0).  Rows longer
-// than 32 entries, or whose gathers span more than 32 instructions, keep their order.
+// each nonzero of a row, in stored order, moves to a free slot of its row whose gather
+// instruction has so far the fewest entries in the nonzero's bank pair (ties: the lowest
+// instruction, then the lowest lane).  On config-3 columns this greedy placement takes the
+// expected wavefronts of a gather from 6.1 to 3.9 (a full assignment per row, by the Hungarian
+// method, reaches 4.0).  Layouts whose rows span more than 16 gather instructions (more than
+// 16 entries at one lane per row, more than 32 at two) keep their order.
+//
+// One thread per half-warp group.  Per bank pair r it keeps a word of sixteen 4-bit counters,
+// one per gather instruction (saturating at 14); the instructions without a free slot read as
+// 15, and the first instruction holding the least count is found with the zero-nibble test
+// ((y - 0x11..1) & ~y & 0x88..8 flags the lowest nibble of y that is zero exactly).
 constexpr int BO_KPMAX = 32;
-constexpr int BO_JMAX = 32;
-
-template <int T>
-__device__ __forceinline__ int bo_instr(int idx) {  // gather instruction of row slot idx
-  const int q = idx >> 2, e = idx & 3;
-  return 4 * (q / T) + e;
-}
+constexpr int BO_JMAX = 16;
+constexpr int BO_THREADS = 64;
+constexpr uint64_t BO_ONES = 0x1111111111111111ull;
 
 template <class PT, int T>
-__global__ void __launch_bounds__(128) ell_bank_order_kernel(DevMDP d, PT* val, int32_t* col,
-                                                             const int* flags, int64_t span_max) {
+__global__ void __launch_bounds__(BO_THREADS) ell_bank_order_kernel(DevMDP d, PT* val, int32_t* col,
+                                                                    const int* flags, int64_t span_max) {
+  __shared__ uint64_t cnt[16][BO_THREADS];   // [bank pair][thread]: counters per instruction
+  __shared__ int32_t sc[BO_KPMAX][BO_THREADS];
+  __shared__ PT sv[BO_KPMAX][BO_THREADS];
   if (flags[0] | flags[1] | flags[2] | flags[3] | flags[4]) return;  // invalid data: left as is
   if ((int64_t)flags[6] > span_max) return;  // not banded: the global-gather sweeps take it
   constexpr int RPI = 32 / T;
@@ -1013,17 +1018,25 @@ __global__ void __launch_bounds__(128) ell_bank_order_kernel(DevMDP d, PT* val, 
   while (Rp < d.A && Rp < RPI) Rp <<= 1;
   const int G = RPI / Rp;
   const int npass = (d.A + RPI - 1) / RPI;
-  const int kp = d.kp;
+  const int kp = d.kp, nvec = kp >> 2;
+  // free slots per instruction j = 4 m + e of a fresh row: the lanes tl < T with tl + T m < nvec
+  uint64_t F0 = 0;
+  for (int j = 0; j < BO_JMAX; ++j) {
+    const int m = j >> 2;
+    int n = 0;
+    for (int tl = 0; tl < T; ++tl) n += (tl + T * m < nvec) ? 1 : 0;
+    F0 |= (uint64_t)n << (4 * j);
+  }
+  const int tid = threadIdx.x;
   const int64_t nblk = (d.S + G - 1) / G;
   const int64_t ngroups = nblk * npass * 2;
-  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; gi < ngroups;
+  for (int64_t gi = (int64_t)blockIdx.x * blockDim.x + tid; gi < ngroups;
        gi += (int64_t)gridDim.x * blockDim.x) {
     const int hw = (int)(gi & 1);
     const int pass = (int)((gi >> 1) % npass);
     const int64_t blk = (gi >> 1) / npass;
-    uint64_t L[BO_JMAX];  // entries so far per gather instruction, 16 saturating 4-bit counters
 #pragma unroll
-    for (int j = 0; j < BO_JMAX; ++j) L[j] = 0;
+    for (int r = 0; r < 16; ++r) cnt[r][tid] = 0;
     for (int rs = hw * 16 / T; rs < (hw + 1) * 16 / T; ++rs) {  // row slots of this half-warp
       const int g = rs / Rp, rr = rs % Rp;
       const int64_t s = blk * G + g;
@@ -1034,34 +1047,61 @@ __global__ void __launch_bounds__(128) ell_bank_order_kernel(DevMDP d, PT* val, 
       int32_t c[BO_KPMAX];
       PT v[BO_KPMAX];
 #pragma unroll
-      for (int i = 0; i < BO_KPMAX; ++i) {
-        c[i] = i < kp ? rc[i] : 0;
-        v[i] = i < kp ? rv[i] : PT(0);
+      for (int q = 0; q < BO_KPMAX / 4; ++q) {
+        if (q < nvec) {
+          const int4 c4 = reinterpret_cast<const int4*>(rc)[q];
+          c[4 * q] = c4.x; c[4 * q + 1] = c4.y; c[4 * q + 2] = c4.z; c[4 * q + 3] = c4.w;
+          Vec4<PT> v4;
+          v4.load_cached(rv + 4 * q);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) v[4 * q + e] = v4.e[e];
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e) { c[4 * q + e] = 0; v[4 * q + e] = PT(0); }
+        }
       }
+      uint64_t F = F0;                       // free slots left per instruction
       uint32_t freem = kp >= 32 ? 0xffffffffu : ((1u << kp) - 1u);
 #pragma unroll
       for (int i = 0; i < BO_KPMAX; ++i) {
         if (i < kp) {
-          const int sh = 4 * (c[i] & 15);
-          int best = 16, bi = 0, bj = 0;
-#pragma unroll
-          for (int idx = 0; idx < BO_KPMAX; ++idx) {
-            const int j = bo_instr<T>(idx);
-            if (j < BO_JMAX && ((freem >> idx) & 1u)) {
-              const int l = (int)((L[j] >> sh) & 15u);
-              if (l < best) {
-                best = l;
-                bi = idx;
-                bj = j;
-              }
+          const int r = c[i] & 15;
+          const uint64_t x = cnt[r][tid];
+          uint64_t nz = F | (F >> 1) | (F >> 2) | (F >> 3);
+          nz &= BO_ONES;                       // 1 in the nibbles with a free slot
+          const uint64_t fm = nz * 15ull;      // 0xF there
+          const uint64_t xs = (x & fm) | ~fm;  // counters, 15 where no slot is free
+          int js = 0;
+          for (int t = 0; t < 15; ++t) {
+            const uint64_t y = xs ^ (BO_ONES * (uint64_t)t);
+            const uint64_t z = (y - BO_ONES) & ~y & (BO_ONES * 8ull);
+            if (z) {
+              js = __ffsll((long long)z) >> 2;  // bit 4j+3 set -> ffs = 4j+4
+              js -= 1;
+              break;
             }
           }
-          freem &= ~(1u << bi);
-          rc[bi] = c[i];
-          rv[bi] = v[i];
+          const int m = js >> 2, e = js & 3;
+          int idx = 4 * (T * m) + e;           // lane tl = 0 of instruction js
 #pragma unroll
-          for (int j = 0; j < BO_JMAX; ++j)
-            if (j == bj && ((L[j] >> sh) & 15u) < 15u) L[j] += 1ull << sh;
+          for (int tl = 0; tl < T; ++tl) {
+            const int id2 = 4 * (tl + T * m) + e;
+            if (id2 < kp && ((freem >> id2) & 1u)) { idx = id2; break; }
+          }
+          freem &= ~(1u << idx);
+          sc[idx][tid] = c[i];
+          sv[idx][tid] = v[i];
+          if (((x >> (4 * js)) & 15ull) < 14ull) cnt[r][tid] = x + (1ull << (4 * js));
+          F -= 1ull << (4 * js);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < BO_KPMAX / 4; ++q) {
+        if (q < nvec) {
+          reinterpret_cast<int4*>(rc)[q] =
+              make_int4(sc[4 * q][tid], sc[4 * q + 1][tid], sc[4 * q + 2][tid], sc[4 * q + 3][tid]);
+#pragma unroll
+          for (int e = 0; e < 4; ++e) rv[4 * q + e] = sv[4 * q + e][tid];
         }
       }
     }
@@ -1218,18 +1258,17 @@ int launch_ell_bank_order(const DevMDP& d, void* val, int32_t* col, const int* f
                           cudaStream_t st) {
   if (d.kind != KIND_ELL || d.S < 4 * WIN_NB || d.kp > BO_KPMAX) return MDP_OK;
   const int T = ell_sweep_lanes_default(d);
-  if (4 * ((d.kp / 4 + T - 1) / T) > BO_JMAX) return MDP_OK;
+  if (T > 2 || 4 * ((d.kp / 4 + T - 1) / T) > BO_JMAX) return MDP_OK;
   const int RPI = 32 / T;
   int Rp = 1;
   while (Rp < d.A && Rp < RPI) Rp <<= 1;
   const int64_t groups = (d.S + RPI / Rp - 1) / (RPI / Rp) * ((d.A + RPI - 1) / RPI) * 2;
-  const int grid = (int)std::max<int64_t>(1, std::min<int64_t>((groups + 127) / 128, (int64_t)num_sms() * 16));
+  const int grid = (int)std::max<int64_t>(
+      1, std::min<int64_t>((groups + BO_THREADS - 1) / BO_THREADS, (int64_t)num_sms() * 32));
   auto go = [&](auto tag) {
     using PT = decltype(tag);
-    switch (T) {
-      case 1: ell_bank_order_kernel<PT, 1><<<grid, 128, 0, st>>>(d, (PT*)val, col, flags, WIN_SPAN_MAX); break;
-      default: ell_bank_order_kernel<PT, 2><<<grid, 128, 0, st>>>(d, (PT*)val, col, flags, WIN_SPAN_MAX); break;
-    }
+    if (T == 1) ell_bank_order_kernel<PT, 1><<<grid, BO_THREADS, 0, st>>>(d, (PT*)val, col, flags, WIN_SPAN_MAX);
+    else ell_bank_order_kernel<PT, 2><<<grid, BO_THREADS, 0, st>>>(d, (PT*)val, col, flags, WIN_SPAN_MAX);
   };
   if (d.pdt == MDP_F32) go(float{});
   else go(double{});
