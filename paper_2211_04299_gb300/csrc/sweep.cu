@@ -844,6 +844,30 @@ __device__ __forceinline__ Pick<AR> ell_state_group(const SweepK& p, const EllLa
     if (need_q2) {
       for (int off = T; off < L.Rp * T; off <<= 1) c = cand_merge<AR>(c, cand_shfl<AR>(c, off));
       run = cand_merge<AR>(run, c);
+    } else if constexpr (Gather::kWindow) {
+      // the least Q of the pass by a butterfly on Q alone, then the lowest lane of this state
+      // group that holds it exactly, allowed rows first (lanes run in action order): the pick of
+      // cand_merge1 (lowest action among the exact minima) with a third of its shuffles, which
+      // share the L1 data pipe with the window gathers.  A NaN anywhere in the warp takes the
+      // full merge.
+      Qt m = c.q;
+      for (int off = T; off < L.Rp * T; off <<= 1) {
+        const Qt o = shfl_xor_q<AR>(m, off);
+        m = AR::lt(o, m) ? o : m;
+      }
+      const int width = L.Rp * T;
+      const unsigned grp = width >= 32 ? 0xffffffffu : (((1u << width) - 1u) << L.leader);
+      const bool eq = !AR::lt(c.q, m) && !AR::lt(m, c.q);
+      const unsigned hit_allowed = __ballot_sync(0xffffffffu, eq && c.a != 0x7fffffff) & grp;
+      const unsigned hit_any = __ballot_sync(0xffffffffu, eq) & grp;
+      if (__any_sync(0xffffffffu, hit_any == 0u)) {
+        for (int off = T; off < L.Rp * T; off <<= 1) c = cand_merge1<AR>(c, cand_shfl1<AR>(c, off));
+      } else {
+        const unsigned hit = hit_allowed ? hit_allowed : hit_any;
+        c.a = __shfl_sync(0xffffffffu, c.a, __ffs(hit) - 1);
+        c.q = m;
+      }
+      run = cand_merge1<AR>(run, c);
     } else {
       for (int off = T; off < L.Rp * T; off <<= 1) c = cand_merge1<AR>(c, cand_shfl1<AR>(c, off));
       run = cand_merge1<AR>(run, c);
