@@ -392,6 +392,37 @@ def test_bellman_banded_window_parity(mg, S, hw, shift, prec):
     h.close()
 
 
+# Lane layouts of the windowed sweep (and of the bank order applied at upload to banded rows):
+# A = 20 with 32 entries per row runs two passes per state at two lanes per row; A = 3 packs
+# four states into a warp pass (each half-warp of the bank order spans two states); k = 16
+# (one lane per row, 16 gather instructions) and k = 20 (20 instructions: rows keep their
+# stored order) close the set.  Ragged S, a solve on the same handle, and a handle built from
+# device arrays (the same bank order) give the same bits.
+@pytest.mark.parametrize("S,A,k", [(5003, 20, 32), (4099, 3, 32), (3001, 7, 16), (2050, 5, 20)])
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+def test_banded_window_lane_layouts(mg, S, A, k, prec):
+    syn = mdp_synth.ell_banded(S, A, k, 400, 30, 0.99, seed=S + A,
+                               val_dtype=np.float32 if prec == "mixed" else np.float64)
+    m = oracle.from_synth(syn)
+    h = mg.from_synth(syn)
+    rng = np.random.default_rng(S + k)
+    v = rng.normal(size=S) * 5.0
+    sw = oracle.bellman(m, v)
+    Tv, pi, res = mg.bellman_apply(h, v, precision=prec)
+    tol = 1e-13 if prec == "fp64" else 1e-12
+    assert rel_err(Tv, sw.Tv) <= tol
+    assert abs(res - sw.res_inf) <= tol * max(1.0, np.max(np.abs(sw.Tv)))
+    check_policy(pi, sw)
+    vs, pis, st = mg.ipi_solve(h, mg.opts(tol=1e-9, precision=prec))
+    assert st["status"] == 0
+    h2 = mg.from_synth(syn, device=True)
+    Tv2, pi2, res2 = mg.bellman_apply(h2, v, precision=prec)
+    np.testing.assert_array_equal(np.asarray(Tv2), np.asarray(Tv))
+    np.testing.assert_array_equal(np.asarray(pi2), np.asarray(pi))
+    h.close()
+    h2.close()
+
+
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_windowed_and_global_sweeps_solve_alike(mg, prec):
     """The windowed sweep gathers the same v values as the global one, so per-state outputs
