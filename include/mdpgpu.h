@@ -69,7 +69,11 @@ int mdp_create_dense(int64_t S, int32_t A, const void* P, int p_dtype, const dou
                      double gamma, const uint8_t* mask, mdp_t* out);
 
 /* ELL-sparse MDP: row (a, s) lists k pairs (col[a][s][j], val[a][s][j]); p_{ss'}(a) is the
- * sum of val over the j with col = s'.  1 <= k <= S, 0 <= col < S, val as P above. */
+ * sum of val over the j with col = s'.  1 <= k <= S, 0 <= col < S, val as P above.
+ * The handle may keep each row's pairs in another order: for banded data (every column within
+ * 1792 states of its row) the pairs are placed to spread the windowed sweep's shared-memory
+ * gathers over the banks.  Only the rounding of each row's sum can change; every solve, batch
+ * and server holding the same MDP uses the same order. */
 int mdp_create_ell(int64_t S, int32_t A, int32_t k, const int32_t* col, const void* val,
                    int val_dtype, const double* g, double gamma, const uint8_t* mask,
                    mdp_t* out);
